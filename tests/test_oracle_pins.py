@@ -1,0 +1,274 @@
+"""Pins for the CPU oracle against facts fixed outside it: hand-derived
+values, closed forms, invariants, brute force and an independent LP solver.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+flipped sign, a transposed operand, a wrong update order) breaks at least one.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import pdhg_oracle as O
+from paper_2603_03150_gb300 import lpgen
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------- a1 transpose
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_transpose_matches_dense_and_is_stable(seed):
+    rng = np.random.default_rng(seed)
+    m, n = 37, 53
+    D = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.15)
+    rows, cols = np.nonzero(D)
+    A = sp.csr_matrix((D[rows, cols], (rows, cols)), shape=(m, n))
+    rp, ci, v = O.transpose_csr(m, n, A.indptr, A.indices, A.data)
+    T = np.zeros((n, m))
+    for j in range(n):
+        T[j, ci[rp[j]:rp[j + 1]]] = v[rp[j]:rp[j + 1]]
+        # stable: the rows of column j come in increasing order
+        assert np.all(np.diff(ci[rp[j]:rp[j + 1]]) > 0)
+    np.testing.assert_array_equal(T, D.T)
+
+
+# --------------------------------------------------------------- a2 scaling
+def test_ruiz_one_round_by_hand():
+    # A = [[4,0],[1,9]]: row max [4,9] -> r=[2,3]; col max [4,9] -> s=[2,3]
+    A = sp.csr_matrix(np.array([[4.0, 0.0], [1.0, 9.0]]))
+    D_r, D_c, At = O.scale(A, ruiz_iters=1, pock_chambolle=False)
+    np.testing.assert_allclose(D_r, [0.5, 1 / 3], rtol=1e-15)
+    np.testing.assert_allclose(D_c, [0.5, 1 / 3], rtol=1e-15)
+    np.testing.assert_allclose(At.toarray(), [[1.0, 0.0], [1 / 6, 1.0]], rtol=1e-15)
+
+
+def test_pock_chambolle_by_hand():
+    # A = [[4,0],[1,9]]: row 1-norms [4,10] -> r=[2,sqrt10]; col 1-norms [5,9] -> s=[sqrt5,3]
+    A = sp.csr_matrix(np.array([[4.0, 0.0], [1.0, 9.0]]))
+    D_r, D_c, At = O.scale(A, ruiz_iters=0, pock_chambolle=True)
+    np.testing.assert_allclose(D_r, [0.5, 1 / np.sqrt(10)], rtol=1e-15)
+    np.testing.assert_allclose(D_c, [1 / np.sqrt(5), 1 / 3], rtol=1e-15)
+    np.testing.assert_allclose(At.toarray(), [[2 / np.sqrt(5), 0.0],
+                                              [1 / np.sqrt(50), 3 / np.sqrt(10)]], rtol=1e-14)
+
+
+def test_scaling_reconstructs_and_equilibrates():
+    lp = lpgen.powerlaw_lp(m=2000, n=10000, nnz=50000, k_max=2000, seed=3)
+    A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+    D_r, D_c, At = O.scale(A, 10, True)
+    R = sp.diags(D_r) @ A @ sp.diags(D_c)
+    np.testing.assert_allclose(At.toarray(), R.toarray(), rtol=1e-12, atol=0)
+    # Ruiz alone drives every row and column infinity norm to 1
+    _, _, Ar = O.scale(A, 10, False)
+    for v in (O._row_absmax(Ar), O._col_absmax(Ar)):
+        assert v.min() >= 1 - 1e-2 and v.max() <= 1 + 1e-12
+    _, _, Ar = O.scale(A, 20, False)
+    for v in (O._row_absmax(Ar), O._col_absmax(Ar)):
+        assert v.min() >= 1 - 1e-4 and v.max() <= 1 + 1e-12
+
+
+def test_scaling_empty_row_and_column_keep_factor_one():
+    A = sp.csr_matrix(np.array([[2.0, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 8.0]]))
+    D_r, D_c, At = O.scale(A, 10, True)
+    assert D_r[1] == 1.0 and D_c[1] == 1.0
+
+
+# --------------------------------------------------------------- a3 step size
+def test_power_iteration_closed_form_diagonal():
+    A = sp.csr_matrix(np.diag([3.0, 1.0, 2.0]))
+    s, k = O.power_iteration(A, 200, 1e-10)
+    assert abs(s - 3.0) < 1e-9 and k < 200
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_power_iteration_vs_svd(seed):
+    lp = lpgen.planted_lp(60, 150, 5, seed=seed)
+    A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+    _, _, At = O.scale(A)
+    s, _ = O.power_iteration(At, 200, 1e-10)
+    true = np.linalg.norm(At.toarray(), 2)
+    assert s <= true * (1 + 1e-12)
+    assert s >= true * (1 - 1e-3)
+
+
+def test_initial_omega():
+    assert O.initial_omega(np.array([3.0, 4.0]), np.array([0.0, 10.0])) == 2.0
+    assert O.initial_omega(np.zeros(2), np.ones(2)) == 1.0
+
+
+# --------------------------------------------------------------- a4/a5 step
+def test_pdhg_step_by_hand():
+    g = _load("small_lp_hand.json")
+    A = sp.csr_matrix(np.array(g["A"]))
+    s = g["step"]
+    x1, y1 = O.pdhg_step(A, np.array(g["b"]), np.array(g["c"]), np.array(s["x"]),
+                         np.array(s["y"]), s["tau"], s["sigma"])
+    np.testing.assert_allclose(x1, s["x_new"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(y1, s["y_new"], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("tau,sigma", [(0.1, 10.0), (1.0, 1.0), (3.0, 0.01)])
+def test_pdhg_fixed_point_at_planted_optimum(tau, sigma):
+    """A strictly complementary optimum is a fixed point of one step for any
+    tau, sigma > 0: on supp(x*), z* = 0 leaves x*; off it, x* - tau z* < 0
+    projects to 0; and b - A x* = 0 leaves y*."""
+    lp = lpgen.planted_lp(200, 500, seed=4)
+    A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+    x1, y1 = O.pdhg_step(A, lp.b, lp.c, lp.x_star, lp.y_star, tau, sigma)
+    np.testing.assert_allclose(x1, lp.x_star, rtol=0, atol=1e-12 * (1 + tau))
+    np.testing.assert_allclose(y1, lp.y_star, rtol=0, atol=1e-12 * (1 + sigma) * 10)
+
+
+# --------------------------------------------------------------- a7 residuals
+def test_kkt_termination_violation_by_hand():
+    g = _load("small_lp_hand.json")
+    A = sp.csr_matrix(np.array(g["A"]))
+    b, c = np.array(g["b"]), np.array(g["c"])
+    k = g["kkt"]
+    assert abs(O.kkt_error(A, b, c, np.array(k["x"]), np.array(k["y"]), k["omega"])
+               - k["value"]) < 1e-13
+    t = g["term"]
+    x, y = np.array(t["x"]), np.array(t["y"])
+    ok1, rp, rd, gap = O.termination_test(A, b, c, x, y, 1.0)
+    ok2 = O.termination_test(A, b, c, x, y, 2.0)[0]
+    assert ok1 == t["converged_eps_1"] and ok2 == t["converged_eps_2"]
+    assert abs(rp - t["r_P"]) < 1e-13 and abs(rd - t["r_D"]) < 1e-13 and abs(gap - t["gap"]) < 1e-13
+    v = g["violation"]
+    assert abs(O.max_violation(A, b, c, np.array(v["x"]), np.array(v["y"])) - v["value"]) < 1e-13
+
+
+def test_optimality_conditions_at_planted_point():
+    """Section 2: at the planted optimum the residuals vanish, x,z >= 0, and
+    the gap c^T x - b^T y vanishes (equivalently x^T z = 0)."""
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+    ok, rp, rd, gap = O.termination_test(A, lp.b, lp.c, lp.x_star, lp.y_star, 1e-12)
+    assert ok and rp < 1e-12 and rd < 1e-12 and gap < 1e-10
+    assert O.max_violation(A, lp.b, lp.c, lp.x_star, lp.y_star) < 1e-12
+
+
+# --------------------------------------------------------------- a9 Algorithm 1
+def test_algorithm1_hand_cases():
+    for case in _load("alg1_cases.json")["cases"]:
+        xp, zp, mu = O.centered_start_point(np.array(case["x"]), np.array(case["z"]),
+                                            case["mu_min"], case["delta_max"], case["alpha_min"])
+        assert abs(mu - case["mu"]) <= 1e-15 * max(1.0, case["mu"]), case["name"]
+        np.testing.assert_allclose(xp, case["x_out"], rtol=1e-12, err_msg=case["name"])
+        np.testing.assert_allclose(zp, case["z_out"], rtol=1e-12, err_msg=case["name"])
+
+
+def test_algorithm1_centering_with_wide_delta():
+    """With delta_max large enough that no clamp binds, the second update of
+    each pair lands exactly on x'_j z'_j = mu_target."""
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0, 2, 400) * (rng.random(400) < 0.5)
+    z = rng.uniform(0, 2, 400) * (rng.random(400) < 0.5)
+    xp, zp, mu = O.centered_start_point(x, z, 1e-6, 1e6, 1e-6)
+    np.testing.assert_allclose(xp * zp, mu, rtol=1e-12)
+    assert np.all(xp > 0) and np.all(zp > 0)
+
+
+# --------------------------------------------------------------- full solve
+def test_solve_planted_small_converges_to_planted_optimum():
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    r = O.solve(lp, 1e-4, 100_000)
+    assert r.status == O.STATUS_CONVERGED
+    A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+    assert O.termination_test(A, lp.b, lp.c, r.x, r.y, 1e-4)[0]
+    assert np.all(r.x >= 0) and np.all(r.z >= 0)
+    obj = float(lp.c @ lp.x_star)
+    assert abs(float(lp.c @ r.x) - obj) <= 1e-4 * (1 + abs(obj))
+    r8 = O.solve(lp, 1e-8, 400_000)
+    assert r8.status == O.STATUS_CONVERGED
+    assert np.max(np.abs(r8.x - lp.x_star)) < 1e-5
+
+
+def _brute_force_vertex_min(A, b, c):
+    m, n = A.shape
+    best = np.inf
+    for B in itertools.combinations(range(n), m):
+        AB = A[:, B]
+        if abs(np.linalg.det(AB)) < 1e-10:
+            continue
+        xB = np.linalg.solve(AB, b)
+        if np.all(xB >= -1e-10):
+            best = min(best, float(c[list(B)] @ xB))
+    return best
+
+
+@pytest.mark.parametrize("m,n,seed", [(3, 7, 0), (4, 9, 1), (5, 10, 2), (6, 12, 3), (4, 8, 4)])
+def test_solve_matches_vertex_enumeration(m, n, seed):
+    lp = lpgen.tiny_feasible_lp(m, n, seed)
+    A = lp.dense()
+    best = _brute_force_vertex_min(A, lp.b, lp.c)
+    r = O.solve(lp, 1e-9, 2_000_000)
+    assert r.status == O.STATUS_CONVERGED
+    assert abs(float(lp.c @ r.x) - best) <= 1e-6 * (1 + abs(best))
+
+
+@pytest.mark.parametrize("m,n,seed", [(4, 9, 10), (5, 11, 11)])
+def test_planted_tiny_matches_vertex_enumeration(m, n, seed):
+    lp = lpgen.planted_lp(m, n, 3, seed=seed, n_pos=2)
+    best = _brute_force_vertex_min(lp.dense(), lp.b, lp.c)
+    assert abs(best - float(lp.c @ lp.x_star)) <= 1e-9 * (1 + abs(best))
+    r = O.solve(lp, 1e-9, 2_000_000)
+    assert abs(float(lp.c @ r.x) - best) <= 1e-6 * (1 + abs(best))
+
+
+def test_solve_matches_highs_on_planted_and_transportation():
+    from scipy.optimize import linprog
+    for lp in (lpgen.planted_lp(200, 500, seed=1), lpgen.transportation_lp(30, 40, seed=0)):
+        A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+        h = linprog(lp.c, A_eq=A, b_eq=lp.b, bounds=(0, None), method="highs")
+        assert h.status == 0
+        r = O.solve(lp, 1e-4, 200_000)
+        assert r.status == O.STATUS_CONVERGED
+        assert abs(float(lp.c @ r.x) - h.fun) <= 2e-4 * (1 + abs(h.fun)), lp.name
+
+
+def test_max_iter_stops_without_restart_and_counts():
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    r = O.solve(lp, 1e-12, 100)
+    assert r.status == O.STATUS_MAX_ITER and r.iters == 100
+    # one evaluation of the restart rule at k = 64 (k = 100 only tests termination)
+    assert [e["k"] for e in r.log] == [64]
+    r2 = O.solve(lp, 1e-12, 128)
+    assert [e["k"] for e in r2.log] == [64]  # k = 128 = max_iter: no restart rule
+
+
+def test_termination_primal_bound_uses_norm_b():
+    g = _load("small_lp_hand.json")
+    A = sp.csr_matrix(np.array(g["A"]))
+    b, c = np.array(g["b"]), np.array(g["c"])
+    t = g["term_primal_binding"]
+    x, y = np.array(t["x"]), np.array(t["y"])
+    ok8, rp, rd, gap = O.termination_test(A, b, c, x, y, 0.8)
+    assert ok8 == t["converged_eps_0.8"]
+    assert O.termination_test(A, b, c, x, y, 0.7)[0] == t["converged_eps_0.7"]
+    assert abs(rp - t["r_P"]) < 1e-13 and rd == t["r_D"] and abs(gap - t["gap"]) < 1e-13
+
+
+def test_running_average_is_mean_of_iterates():
+    """Before the first evaluation the averages are the plain means of the
+    iterates x^1..x^k, y^1..y^k produced by repeated single steps."""
+    lp = lpgen.planted_lp(200, 500, seed=2)
+    S = O.setup(lp)
+    r = O.solve(lp, 1e-12, 50, S=S)
+    tau, sigma = S.eta / S.omega0, S.eta * S.omega0
+    x, y = np.zeros(lp.n), np.zeros(lp.m)
+    xs, ys = [], []
+    for _ in range(50):
+        x, y = O.pdhg_step(S.At, S.b_t, S.c_t, x, y, tau, sigma)
+        xs.append(x)
+        ys.append(y)
+    np.testing.assert_allclose(r.state.x, x, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(r.state.x_avg, np.mean(xs, axis=0), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r.state.y_avg, np.mean(ys, axis=0), rtol=0, atol=1e-12)
