@@ -1,0 +1,182 @@
+/*
+ * pdhg.h -- C ABI of the GB300 restarted-PDHG library (libpdhg.so).
+ *
+ * Problem (Section 2 of "Hybridizing PDHG and Interior-Point Methods"):
+ *     primal  min c^T x   s.t.  A x = b,  x >= 0        (A is m x n)
+ *     dual    max b^T y   s.t.  A^T y + z = c,  z >= 0
+ * with residuals r_P = b - A x, r_D = c - A^T y - z and the relative
+ * termination test of Section 2:
+ *     ||r_P||_2 <= eps (1 + ||b||_2),  ||r_D||_2 <= eps (1 + ||c||_2),
+ *     |c^T x - b^T y| <= eps (1 + |c^T x| + |b^T y|).
+ * For a PDHG iterate the library takes z = max(0, c - A^T y).
+ *
+ * The iteration, scaling, step size and restart rule are a stated reading of
+ * the paper's "PDHG following cuPDLP+" (Section 4.1); Algorithm 1 (Section
+ * 3.1) is computed on device by pdhg_warmstart_point.
+ *
+ * Conventions for every entry point:
+ *  - Return value: a pdhg_status.  Negative values mean the call failed and
+ *    the context (if any) must only be destroyed; pdhg_last_error() then
+ *    holds a message (thread-local, valid until the next call on the thread).
+ *  - Array arguments are borrowed for the duration of the call and copied;
+ *    the caller keeps ownership.  They are HOST pointers unless the context
+ *    was created with options.io_on_device = 1, in which case they are
+ *    device pointers on this GPU, read and written in order on
+ *    options.stream.  A NULL output pointer is skipped.
+ *  - Outputs are float64 in the original (unscaled) model unless stated.
+ *  - No C++ exception or process exit crosses this boundary.
+ *  - A context is not thread-safe; distinct contexts may be used from
+ *    distinct threads on distinct streams.
+ */
+#ifndef PDHG_H
+#define PDHG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdhg_ctx pdhg_ctx;
+
+typedef enum pdhg_status {
+  PDHG_OK = 0,
+  PDHG_CONVERGED = 0,        /* termination test met                         */
+  PDHG_MAX_ITER = 1,         /* iteration limit reached first                */
+  PDHG_NUMERICAL_ERROR = 2,  /* NaN/Inf met in the iterate or the residuals  */
+  PDHG_TIMEOUT = 3,          /* a bounded device wait gave up                */
+  PDHG_INVALID_ARG = -1,
+  PDHG_CUDA_ERROR = -2,
+  PDHG_OOM = -3
+} pdhg_status;
+
+enum { PDHG_FP64 = 0, PDHG_FP32_MIXED = 1 };
+
+typedef struct pdhg_options {
+  int32_t precision;       /* PDHG_FP64 (default) or PDHG_FP32_MIXED: A~ and the
+                              iterates in float32 with float32-accumulated SpMV;
+                              norms, gap, restart rule and step/weight updates in
+                              float64 */
+  int32_t eval_freq;       /* F: iterations between evaluations (default 64)    */
+  int32_t ruiz_iters;      /* Ruiz infinity-norm rounds (default 10)            */
+  int32_t pock_chambolle;  /* 1: one Pock-Chambolle step after Ruiz (default 1) */
+  double eta_safety;       /* eta = eta_safety / sigma_max(A~) (default 0.95)   */
+  int32_t power_max_iter;  /* power-iteration limit (default 200)               */
+  double power_rel_tol;    /* power-iteration stop on rel. change (1e-10)       */
+  double beta_sufficient;  /* restart if KKT <= 0.2 KKT(last restart)           */
+  double beta_necessary;   /* ... or <= 0.8 KKT(last) and no progress           */
+  double beta_artificial;  /* ... or iterations since restart >= 0.36 k         */
+  double theta;            /* primal-weight smoothing (0.5)                     */
+  int32_t io_on_device;    /* 1: every array argument is a device pointer       */
+  void* stream;            /* cudaStream_t to run on; NULL: a library stream    */
+  int32_t use_graphs;      /* 1 (default): replay each F-iteration chunk as a
+                              CUDA graph                                        */
+  int32_t autotune;        /* 1 (default): time SpMV tile schedules at create   */
+  int32_t tile_nnz;        /* >0: fixed nonzeros per SpMV tile (no autotune)    */
+  int32_t kernel_timing;   /* 1: sample primal/dual kernel durations with CUDA
+                              events during pdhg_solve                          */
+  int32_t verbose;
+} pdhg_options;
+
+/* Fill *opt with the defaults listed above. */
+void pdhg_default_options(pdhg_options* opt);
+
+/* Create a solver context for one LP (Section 2 standard form).
+ *  m, n       rows and columns of A (m >= 1, n >= 1)
+ *  row_ptr    int32[m+1], row_ptr[0] = 0, non-decreasing, nnz = row_ptr[m]
+ *  col        int32[nnz], strictly increasing within each row, in [0, n)
+ *  val        float64[nnz], finite
+ *  b, c       float64[m], float64[n], finite
+ *  opt        NULL for defaults
+ * On device: builds A^T (stable by row), scales (Ruiz + Pock-Chambolle),
+ * estimates sigma_max(A~) by power iteration, sets omega_0 = ||c~||/||b~||,
+ * and starts from x = 0, y = 0.  Invalid CSR -> PDHG_INVALID_ARG.  */
+pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const int32_t* row_ptr,
+                        const int32_t* col, const double* val, const double* b,
+                        const double* c, const pdhg_options* opt);
+
+/* Run restarted PDHG from the context's current state until the Section 2
+ * test holds with eps = eps_rel (evaluated every F iterations, on the current
+ * iterate first, then the running average) or the cumulative iteration count
+ * reaches max_iter.  Returns PDHG_CONVERGED, PDHG_MAX_ITER or an error.  */
+pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_iter);
+
+/* The returned iterate (the one that passed the test, else the current one)
+ * in the original model: x[n], y[m], z[n] = max(0, c - A^T y), and
+ * ||r_P||_2, ||r_D||_2, |c^T x - b^T y|, all evaluated in float64.  */
+pdhg_status pdhg_get(pdhg_ctx* ctx, double* x, double* y, double* z, double* r_P,
+                     double* r_D, double* gap);
+
+/* Iterations done, restarts taken, the Section 4.3 maximum violation
+ * max(||r_P||_inf, ||r_D||_inf, x^T z / (1 + |c^T x|)) of the returned
+ * iterate, whether it is the running average (1) or the current iterate (0),
+ * and the status of the last pdhg_solve.  */
+pdhg_status pdhg_get_info(pdhg_ctx* ctx, int64_t* iters, int64_t* restarts,
+                          double* max_violation, int32_t* chosen_average,
+                          int32_t* last_status);
+
+/* Algorithm 1, lines 2-11 (Section 3.1), computed on device on the scaled
+ * returned iterate (x~, y~, z~ = max(0, c~ - A~^T y~)):
+ *   mu = max(x~^T z~ / n, mu_min); per j lift to alpha_min, then move the
+ *   smaller of the pair toward mu / (other) within +-delta_max, then the
+ *   other toward mu / (updated first); a tie moves z' first.
+ * Outputs x_ws[n], y_ws[m], z_ws[n] in the scaled model, or mapped back to
+ * the original model (x = D_c x', y = D_r y~, z = z' / D_c) if unscaled = 1;
+ * *mu_target receives mu.  The paper's values: mu_min = alpha_min = 1e-6,
+ * delta_max = 1e-4.  */
+pdhg_status pdhg_warmstart_point(pdhg_ctx* ctx, double mu_min, double delta_max,
+                                 double alpha_min, int32_t unscaled, double* x_ws,
+                                 double* y_ws, double* z_ws, double* mu_target);
+
+/* Scaling and step data: D_r[m], D_c[n] (A~ = D_r A D_c), sigma_max(A~)
+ * estimate, eta, omega_0 and the power iterations taken.  */
+pdhg_status pdhg_get_scaling(pdhg_ctx* ctx, double* D_r, double* D_c, double* sigma_max,
+                             double* eta, double* omega0, int32_t* power_iters);
+
+/* The stored transpose with the ORIGINAL values: row_ptr_t[n+1],
+ * col_t[nnz] (row indices of A, increasing within each row of A^T),
+ * val_t[nnz].  */
+pdhg_status pdhg_get_transpose(pdhg_ctx* ctx, int32_t* row_ptr_t, int32_t* col_t,
+                               double* val_t);
+
+/* Checkpoint: scaled iterate x[n], y[m], running averages, last restart point,
+ * and scalars[8] = {omega, k, t, restarts, kkt_last, kkt_prev, eta, 0}.
+ * pdhg_set_state restores the same fields (Ax caches are recomputed).  */
+pdhg_status pdhg_get_state(pdhg_ctx* ctx, double* x, double* y, double* x_avg,
+                           double* y_avg, double* x_last, double* y_last, double* scalars);
+pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const double* y,
+                           const double* x_avg, const double* y_avg, const double* x_last,
+                           const double* y_last, const double* scalars);
+
+/* Evaluation log of the restart rule (one entry per evaluation with k % F == 0
+ * that did not terminate; up to `cap` entries, oldest first):
+ *   k[i]; flags[i] = restart | cand_is_average << 1 | r1 << 2 | r2 << 3 | r3 << 4;
+ *   kkt[3 i + 0..2] = KKT(current), KKT(average), omega at evaluation.  */
+pdhg_status pdhg_get_log(pdhg_ctx* ctx, int32_t cap, int32_t* count, int64_t* k,
+                         int32_t* flags, double* kkt);
+
+/* With options.kernel_timing = 1: mean duration (ms) of the sampled primal
+ * (A^T y + projection) and dual (A x + dual step) kernel launches of the last
+ * pdhg_solve, and the number of samples of each.  */
+pdhg_status pdhg_get_kernel_timing(pdhg_ctx* ctx, double* primal_ms, double* dual_ms,
+                                   int64_t* samples);
+
+/* Tile schedule picked for A (dual kernel) and A^T (primal kernel):
+ * nonzeros per tile, threads per block, tiles, grid size.  */
+pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int32_t* a_block,
+                              int32_t* a_tiles, int32_t* at_tile_nnz, int32_t* at_block,
+                              int32_t* at_tiles);
+
+/* Kernels this context has launched since pdhg_create (graph replays count
+ * every kernel node).  */
+pdhg_status pdhg_get_launch_count(pdhg_ctx* ctx, int64_t* launches);
+
+void pdhg_destroy(pdhg_ctx* ctx);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* pdhg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDHG_H */

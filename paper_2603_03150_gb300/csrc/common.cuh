@@ -1,0 +1,142 @@
+// Shared device-side definitions for the restarted-PDHG kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pdhg {
+
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------------------
+// CSR tile schedule.  A tile is a run of whole rows whose nonzeros fit in
+// `tile_nnz`, or one chunk of a row longer than that ("split row").  A split
+// row's chunks form a group: each chunk writes its partial sum to a slot, and
+// the chunk that arrives last (atomic ticket) adds the slots in chunk order
+// and runs the row epilogue, so the sum order is fixed.
+// ---------------------------------------------------------------------------
+struct Tile {
+  int32_t row_begin, row_end;  // rows [row_begin, row_end)
+  int32_t nz_begin, nz_end;    // nonzeros [nz_begin, nz_end)
+  int32_t split;               // -1: whole rows; else split-group index
+  int32_t part;                // chunk index within the split group
+  int32_t lanes;               // threads per row in the reduction (power of 2)
+  int32_t pad;
+};
+
+struct SplitGroup {
+  int32_t row;
+  int32_t nparts;
+  int32_t slot0;  // first slot of this group in the slot array
+  int32_t pad;
+};
+
+struct SchedView {
+  const Tile* tiles;
+  const SplitGroup* groups;
+  int32_t* counters;  // [ngroups], zero between launches
+  void* slots;        // [total parts * NV] partial sums
+  int32_t ntiles;
+  int32_t tile_nnz;
+  int32_t max_rows;
+  int32_t ngroups;   // split groups (records appended after block partials)
+};
+
+// ---------------------------------------------------------------------------
+// Device-resident solver scalars (float64 state of the restart rule).
+// ---------------------------------------------------------------------------
+enum { Q_S1 = 0,  // ||b~ - A~x||^2            (scaled primal residual)
+       Q_S2,      // ||min(0, c~ - A~^T y)||^2  (scaled dual residual)
+       Q_S3,      // c~^T x~ (= c^T x)
+       Q_S4,      // b~^T y~ (= b^T y)
+       Q_U1,      // ||b - Ax||^2  (original model)
+       Q_U2,      // ||min(0, c - A^T y)||^2 (original model)
+       Q_D1,      // ||x~ - x~_last||^2
+       Q_D2,      // ||y~ - y~_last||^2
+       Q_N };
+
+struct Scalars {
+  double omega, tau, sigma, eta;
+  double kkt_last, kkt_prev;
+  double norm_b, norm_c;        // original-model norms
+  double eps;
+  double beta_suff, beta_nec, beta_art, theta;
+  double q[2][Q_N];             // last evaluation, [0] current, [1] average
+  long long k, t, restarts, max_iter;
+  int32_t eval_freq;
+  int32_t done;                 // solve finished (kernels become no-ops)
+  int32_t status;               // pdhg_status of the solve
+  int32_t chosen_avg;           // returned iterate is the running average
+  int32_t restart_pending;      // restart_apply must act
+  int32_t restart_to_avg;       // ... with the average as the new iterate
+  int32_t log_count, log_cap;
+  int32_t ticket;               // last-block-done counter for the eval kernel
+  int32_t pad;
+};
+
+struct PowerState {
+  double lam, lam_prev, inv_norm;
+  int32_t k, max_iter, stopped, ticket;
+  double rel_tol;
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce `nq` doubles per thread over the block; result valid in thread 0's
+// `out`.  `red` holds nq * (BLOCK / 32) doubles of shared memory.
+template <int BLOCK, int NQ>
+__device__ __forceinline__ void block_sum(const double (&v)[NQ], double (&out)[NQ], double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double s = warp_sum(v[q]);
+    if (lane == 0) red[q * (BLOCK / 32) + w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int i = 0; i < BLOCK / 32; ++i) s += red[q * (BLOCK / 32) + i];
+      out[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  float v[4];
+  __device__ __forceinline__ void load(const float* p) {
+    float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ __forceinline__ void store_smem(float* p) const {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Vec4<double> {
+  double v[4];
+  __device__ __forceinline__ void load(const double* p) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ __forceinline__ void store_smem(double* p) const {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+__device__ __forceinline__ int4 ldg_int4(const int32_t* p) {
+  return __ldg(reinterpret_cast<const int4*>(p));
+}
+
+}  // namespace pdhg

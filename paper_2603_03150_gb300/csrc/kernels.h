@@ -1,0 +1,135 @@
+// Host-side launchers for the PDHG kernels (implemented in *_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace pdhg {
+
+constexpr int kBlock = 256;       // threads per block of every tile kernel
+constexpr int kEvalQ = 2 * Q_N;   // reduced quantities per evaluation
+
+// Device pointers of one LP's iteration state in precision T.
+template <typename T>
+struct IterBuffers {
+  const int32_t *a_rp, *a_col;  // A~ (rows = m)
+  const T* a_val;
+  const int32_t *t_rp, *t_col;  // A~^T (rows = n)
+  const T* t_val;
+  SchedView a_sched, t_sched;
+  T *x, *y, *x_avg, *y_avg, *x_last, *y_last, *Ax, *Ax_avg;
+  const T *c_t, *b_t;                       // scaled c, b in precision T
+  const double *c_t64, *b_t64, *D_r, *D_c;  // float64 copies and scalings
+  Scalars* sc;
+  double* partials;    // [grid][kEvalQ]
+  double* split_q;     // [split groups of A^T][kEvalQ]
+  long long* log_k;
+  int32_t* log_flags;
+  double* log_kkt;
+  int32_t m, n;
+};
+
+struct Launch {
+  int grid;
+  size_t smem;
+};
+
+// one PDHG iteration, iteration index i within the current chunk
+template <typename T>
+void launch_primal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
+template <typename T>
+void launch_dual(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
+// evaluation after `chunk` iterations + on-device restart/termination rule
+template <typename T>
+void launch_eval(const IterBuffers<T>& B, const Launch& L, int chunk, cudaStream_t s);
+template <typename T>
+void launch_restart(const IterBuffers<T>& B, int grid, cudaStream_t s);
+
+// Pure SpMV (out = M v) over a schedule, used by the autotuner and power
+// iteration.  T = float or double.
+template <typename T>
+void launch_spmv(const SchedView& S, const int32_t* rp, const int32_t* col, const T* val,
+                 const T* v, T* out, const Launch& L, cudaStream_t s);
+
+// float64 report of an iterate (x~, y~ given in float64):
+//   part n: z, x outputs and partials [grid][4] = {U2, S3, XZ, inf_rd}
+//   part m: y output and partials [grid][4] = {U1, S4, 0, inf_rp}
+void launch_report_n(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
+                     const double* x_s, const double* y_s, const double* c_t, const double* D_c,
+                     double* x_out, double* z_out, double* partials, const Launch& L, cudaStream_t s);
+void launch_report_m(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
+                     const double* x_s, const double* y_s, const double* b_t, const double* D_r,
+                     double* y_out, double* partials, const Launch& L, cudaStream_t s);
+// sums the two partial sets into out[8] = {r_P, r_D, gap, maxviol, c^T x, b^T y, x^T z, 0}
+void launch_report_final(const double* pn, int gn, const double* pm, int gm, double* out,
+                         cudaStream_t s);
+
+// Algorithm 1 (Section 3.1)
+void launch_ws_z(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
+                 const double* x_s, const double* y_s, const double* c_t, double* z_s,
+                 double* partials, const Launch& L, cudaStream_t s);
+void launch_ws_mu(const double* partials, int g, int n, double mu_min, double* mu, cudaStream_t s);
+void launch_ws_apply(int n, int m, const double* x_s, const double* z_s, const double* y_s,
+                     const double* mu, double delta_max, double alpha_min, int unscaled,
+                     const double* D_r, const double* D_c, double* x_out, double* y_out,
+                     double* z_out, cudaStream_t s);
+
+// conversions and elementwise helpers
+void launch_convert_d2f(const double* src, float* dst, int64_t len, cudaStream_t s);
+void launch_convert_f2d(const float* src, double* dst, int64_t len, cudaStream_t s);
+
+// ---- setup (setup_kernels.cu) -------------------------------------------
+void launch_validate(int m, int n, const int32_t* rp, const int32_t* col, const double* val,
+                     const double* b, const double* c, int32_t* flags, cudaStream_t s);
+void launch_col_hist(int64_t nnz, const int32_t* col, int32_t* cnt, cudaStream_t s);
+// exclusive scan of cnt[len] into out[len+1]; tmp holds >= len/1024 + 2 ints
+void launch_scan(const int32_t* cnt, int32_t* out, int len, int32_t* tmp, cudaStream_t s);
+void launch_scatter(int m, const int32_t* rp, const int32_t* col, const double* val,
+                    int32_t* cursor, int32_t* col_t, double* val_t, cudaStream_t s);
+void launch_segsort(int nseg, const int32_t* seg_ptr, int32_t* keys, double* vals,
+                    const int32_t* long_ids, int n_long, int32_t* tmp_k, double* tmp_v,
+                    cudaStream_t s);
+// Ruiz / Pock-Chambolle statistic of each row of D_self M D_other:
+// mode 0: sqrt(max |.|), mode 1: sqrt(sum |.|); zero -> 1.
+void launch_row_stat(int nrows, const int32_t* rp, const int32_t* col, const double* val,
+                     const double* d_self, const double* d_other, int mode, double* out,
+                     cudaStream_t s);
+void launch_div(double* d, const double* r, int len, cudaStream_t s);
+void launch_fill(double* d, double v, int64_t len, cudaStream_t s);
+// A~_ij = (D_r[i] A_ij) D_c[j]; transposed = 1 when the rows are columns of A
+void launch_scale_vals(int nrows, const int32_t* rp, const int32_t* col, const double* val,
+                       const double* D_r, const double* D_c, int transposed, double* out64,
+                       float* out32, cudaStream_t s);
+void launch_scale_vec(int len, const double* d, const double* v, double* out64, float* out32,
+                      cudaStream_t s);
+// partial sums (mode 0: a.b, 1: |a|^2, 2: |min(0,a)|^2) into partials[grid];
+// then a one-thread total in fixed order
+void launch_dot_partials(int64_t len, const double* a, const double* b, int mode,
+                         double* partials, int grid, cudaStream_t s);
+void launch_sum_final(const double* partials, int g, double* out, cudaStream_t s);
+// power iteration pieces (float64)
+void launch_pow_init(int n, double* v, PowerState* ps, int max_iter, double rel_tol,
+                     cudaStream_t s);
+void launch_pow_ATu(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
+                    const double* u, const double* v, double* w, double* partials,
+                    PowerState* ps, const Launch& L, cudaStream_t s);
+void launch_pow_Av(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
+                   const double* v, double* u, PowerState* ps, const Launch& L, cudaStream_t s);
+void launch_pow_norm(int n, const double* w, double* v, PowerState* ps, cudaStream_t s);
+// scalar set-up of the solve from reduced values
+//   sums[5] = |b|^2, |c|^2, |b~|^2, |c~|^2, |min(0, c~)|^2
+// eta = eta_safety / sigma_max, omega_0 = |c~|/|b~| (1 if either is 0),
+// tau, sigma, and the first restart point (0, 0): kkt_last = kkt_prev =
+// KKT_omega0(0, 0) = sqrt(omega^2 |b~|^2 + |min(0,c~)|^2 / omega^2)
+void launch_init_scalars(Scalars* sc, const double* sums, const PowerState* ps,
+                         double eta_safety, cudaStream_t s);
+cudaError_t configure_setup_kernels(size_t max_smem);
+cudaError_t configure_tile_kernels(size_t max_smem);
+int tile_occupancy(int which, size_t smem);
+size_t tile_smem_1f(int tn, int mr);
+size_t tile_smem_1d(int tn, int mr);
+size_t tile_smem_2f(int tn, int mr);
+size_t tile_smem_2d(int tn, int mr);
+
+}  // namespace pdhg

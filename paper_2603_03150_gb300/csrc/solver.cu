@@ -1,0 +1,1185 @@
+// Host runtime of the single-LP solver behind the C ABI in include/pdhg.h:
+// context set-up, the CSR tile scheduler and its autotuner, the chunked
+// solve loop (CUDA-graph replay, status polled one chunk behind), and the
+// getters.  All arithmetic of the method runs in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "pdhg.h"
+
+namespace pdhg {
+void set_error(const char* fmt, ...);
+}
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void pdhg::set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+using pdhg::set_error;
+
+extern "C" const char* pdhg_last_error(void) { return g_last_error.c_str(); }
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                __LINE__);                                                          \
+      return e_ == cudaErrorMemoryAllocation ? PDHG_OOM : PDHG_CUDA_ERROR;          \
+    }                                                                               \
+  } while (0)
+
+#define CKS(expr)                          \
+  do {                                     \
+    pdhg_status s_ = (expr);               \
+    if (s_ < 0) return s_;                 \
+  } while (0)
+
+namespace pdhg {
+
+// ---------------------------------------------------------------------------
+// tile schedule (host build + device copy)
+// ---------------------------------------------------------------------------
+struct HostSched {
+  std::vector<Tile> tiles;
+  std::vector<SplitGroup> groups;
+  int total_parts = 0;
+  int tile_nnz = 0, max_rows = 0;
+};
+
+static int pow2_floor(int v) {
+  int p = 1;
+  while (p * 2 <= v) p *= 2;
+  return p;
+}
+static int pow2_ceil(int v) {
+  int p = 1;
+  while (p < v) p *= 2;
+  return p;
+}
+
+// threads per row: spread the block over the tile's rows, but no wider than
+// the mean row length needs
+static int lanes_for(int nrows, int64_t nnz) {
+  if (nrows <= 0) return 1;
+  const int by_rows = pow2_floor(std::max(1, kBlock / nrows));
+  const int mean = (int)std::max<int64_t>(1, (nnz + nrows - 1) / nrows);
+  const int by_len = pow2_ceil(mean);
+  return std::max(1, std::min(by_rows, std::min(by_len, kBlock)));
+}
+
+static HostSched build_sched(const int32_t* rp, int nrows, int tile_nnz) {
+  HostSched h;
+  h.tile_nnz = tile_nnz;
+  h.max_rows = tile_nnz;
+  int r = 0;
+  while (r < nrows) {
+    const int64_t len = (int64_t)rp[r + 1] - rp[r];
+    if (len > tile_nnz) {
+      const int nparts = (int)((len + tile_nnz - 1) / tile_nnz);
+      const int gid = (int)h.groups.size();
+      h.groups.push_back(SplitGroup{r, nparts, h.total_parts, 0});
+      for (int p = 0; p < nparts; ++p) {
+        const int64_t b = rp[r] + (int64_t)p * tile_nnz;
+        const int64_t e = std::min<int64_t>(b + tile_nnz, rp[r + 1]);
+        h.tiles.push_back(Tile{r, r + 1, (int32_t)b, (int32_t)e, gid, p, kBlock, 0});
+      }
+      h.total_parts += nparts;
+      ++r;
+      continue;
+    }
+    const int start = r;
+    int64_t nz = 0;
+    while (r < nrows && r - start < h.max_rows) {
+      const int64_t l = (int64_t)rp[r + 1] - rp[r];
+      if (l > tile_nnz || nz + l > tile_nnz) break;
+      nz += l;
+      ++r;
+    }
+    const int nr = r - start;
+    h.tiles.push_back(Tile{start, r, rp[start], rp[r], -1, 0, lanes_for(nr, nz), 0});
+  }
+  return h;
+}
+
+struct DevSched {
+  Tile* tiles = nullptr;
+  SplitGroup* groups = nullptr;
+  int32_t* counters = nullptr;
+  double* slots = nullptr;
+  SchedView view{};
+};
+
+}  // namespace pdhg
+
+using namespace pdhg;
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct pdhg_ctx {
+  int m = 0, n = 0;
+  int64_t nnz = 0, nnz_pad = 0;
+  pdhg_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int nsm = 0;
+  size_t smem_optin = 0;
+  bool mixed = false;
+
+  std::vector<void*> allocs;
+  // matrices
+  int32_t *a_rp = nullptr, *a_col = nullptr, *t_rp = nullptr, *t_col = nullptr;
+  double *a_val_orig = nullptr, *t_val_orig = nullptr, *a_val64 = nullptr, *t_val64 = nullptr;
+  float *a_val32 = nullptr, *t_val32 = nullptr;
+  std::vector<int32_t> h_a_rp, h_t_rp;
+  // vectors
+  double *b = nullptr, *c = nullptr, *b_t64 = nullptr, *c_t64 = nullptr, *D_r = nullptr,
+         *D_c = nullptr;
+  float *b_t32 = nullptr, *c_t32 = nullptr;
+  void *x = nullptr, *y = nullptr, *x_avg = nullptr, *y_avg = nullptr, *x_last = nullptr,
+       *y_last = nullptr, *Ax = nullptr, *Ax_avg = nullptr;
+  double *xs64 = nullptr, *ys64 = nullptr, *out_n1 = nullptr, *out_n2 = nullptr,
+         *out_m1 = nullptr, *report = nullptr, *sums = nullptr;
+  Scalars* sc = nullptr;
+  PowerState* ps = nullptr;
+  double* partials = nullptr;  // generic reduction scratch
+  size_t partials_len = 0;
+  double* split_q = nullptr;
+  long long* log_k = nullptr;
+  int32_t* log_flags = nullptr;
+  double* log_kkt = nullptr;
+  int log_cap = 4096;
+  // schedules and launch shapes
+  DevSched sa, st;
+  Launch l_prim{}, l_dual{}, l_eval{}, l_a64{}, l_t64{};
+  int restart_grid = 1;
+  // graphs and polling
+  cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  cudaEvent_t ev_k[2][4] = {};
+  Scalars* h_sc[2] = {nullptr, nullptr};
+  double timing_sum[2] = {0, 0};
+  long long timing_n = 0;
+  // cached host data
+  double omega0 = 1.0;
+  int power_iters = 0;
+  double report_h[8] = {0};
+  long long launches = 0;  // kernels launched (graph replays count every node)
+  bool report_valid = false;
+  int last_status = PDHG_MAX_ITER;
+};
+
+template <typename T>
+static pdhg_status dalloc(pdhg_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PDHG_OOM : PDHG_CUDA_ERROR;
+  }
+  ctx->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return PDHG_OK;
+}
+
+static pdhg_status copy_in(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return PDHG_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes,
+                     ctx->opt.io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     ctx->stream));
+  return PDHG_OK;
+}
+static pdhg_status copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (!dst || bytes == 0) return PDHG_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes,
+                     ctx->opt.io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  return PDHG_OK;
+}
+
+static size_t smem_for(int kind, bool mixed, int tile_nnz, int max_rows) {
+  // kind 0: NV = 1 in iteration precision, 1: NV = 2 in iteration precision,
+  // 2: NV = 1 float64
+  if (kind == 0) return mixed ? tile_smem_1f(tile_nnz, max_rows) : tile_smem_1d(tile_nnz, max_rows);
+  if (kind == 1) return mixed ? tile_smem_2f(tile_nnz, max_rows) : tile_smem_2d(tile_nnz, max_rows);
+  return tile_smem_1d(tile_nnz, max_rows);
+}
+
+static pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) {
+  *d = DevSched{};
+  CKS(dalloc(ctx, &d->tiles, h.tiles.size()));
+  CKS(dalloc(ctx, &d->groups, h.groups.size()));
+  CKS(dalloc(ctx, &d->counters, h.groups.size()));
+  CKS(dalloc(ctx, &d->slots, (size_t)h.total_parts * 2));
+  if (!h.tiles.empty())
+    CK(cudaMemcpyAsync(d->tiles, h.tiles.data(), h.tiles.size() * sizeof(Tile),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  if (!h.groups.empty())
+    CK(cudaMemcpyAsync(d->groups, h.groups.data(), h.groups.size() * sizeof(SplitGroup),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(d->counters, 0, std::max<size_t>(h.groups.size(), 1) * sizeof(int32_t),
+                     ctx->stream));
+  d->view.tiles = d->tiles;
+  d->view.groups = d->groups;
+  d->view.counters = d->counters;
+  d->view.slots = d->slots;
+  d->view.ntiles = (int32_t)h.tiles.size();
+  d->view.tile_nnz = h.tile_nnz;
+  d->view.max_rows = h.max_rows;
+  d->view.ngroups = (int32_t)h.groups.size();
+  // make the host vectors' lifetime irrelevant: copies are enqueued, wait here
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+static Launch make_launch(pdhg_ctx* ctx, int occ_kind, size_t smem, int ntiles) {
+  const int occ = tile_occupancy(occ_kind, smem);
+  int grid = std::min(ntiles, ctx->nsm * occ);
+  return Launch{std::max(grid, 1), smem};
+}
+
+// Time one SpMV schedule candidate (mean of a few launches after warm-up).
+static pdhg_status time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float* ms_out) {
+  const size_t smem = smem_for(0, ctx->mixed, d.view.tile_nnz, d.view.max_rows);
+  Launch L = make_launch(ctx, ctx->mixed ? 0 : 1, smem, d.view.ntiles);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int warm = 2, reps = 5;
+  ctx->launches += warm + reps;
+  for (int it = 0; it < warm + reps; ++it) {
+    if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
+    if (ctx->mixed) {
+      if (on_a)
+        launch_spmv<float>(d.view, ctx->a_rp, ctx->a_col, ctx->a_val32, (const float*)ctx->x,
+                           (float*)ctx->Ax, L, ctx->stream);
+      else
+        launch_spmv<float>(d.view, ctx->t_rp, ctx->t_col, ctx->t_val32, (const float*)ctx->y,
+                           (float*)ctx->x_last, L, ctx->stream);
+    } else {
+      if (on_a)
+        launch_spmv<double>(d.view, ctx->a_rp, ctx->a_col, ctx->a_val64, (const double*)ctx->x,
+                            (double*)ctx->Ax, L, ctx->stream);
+      else
+        launch_spmv<double>(d.view, ctx->t_rp, ctx->t_col, ctx->t_val64, (const double*)ctx->y,
+                            (double*)ctx->x_last, L, ctx->stream);
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, ctx->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms / reps;
+  return PDHG_OK;
+}
+
+static pdhg_status choose_schedules(pdhg_ctx* ctx) {
+  std::vector<int> cands;
+  if (ctx->opt.tile_nnz > 0)
+    cands.push_back(ctx->opt.tile_nnz);
+  else if (ctx->opt.autotune)
+    cands = {512, 1024, 2048, 4096};
+  else
+    cands = {2048};
+  for (int which = 0; which < 2; ++which) {
+    const bool on_a = which == 0;
+    const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
+    const int nrows = on_a ? ctx->m : ctx->n;
+    DevSched best{};
+    float best_ms = 1e30f;
+    for (int tn : cands) {
+      HostSched h = build_sched(rp.data(), nrows, tn);
+      DevSched d;
+      CKS(upload_sched(ctx, h, &d));
+      float ms = 0.f;
+      if (cands.size() > 1) CKS(time_spmv(ctx, d, on_a, &ms));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = d;
+      }
+    }
+    (on_a ? ctx->sa : ctx->st) = best;
+  }
+  // launch shapes
+  const bool mx = ctx->mixed;
+  const SchedView &A = ctx->sa.view, &T = ctx->st.view;
+  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, smem_for(0, mx, T.tile_nnz, T.max_rows), T.ntiles);
+  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, smem_for(0, mx, A.tile_nnz, A.max_rows), A.ntiles);
+  {
+    const size_t sm = smem_for(1, mx, T.tile_nnz, T.max_rows);
+    const int occ = tile_occupancy(mx ? 4 : 5, sm);
+    // the eval kernel also walks the m rows elementwise: at least enough blocks for that
+    int grid = std::max(T.ntiles, (ctx->m + kBlock - 1) / kBlock);
+    grid = std::max(1, std::min(grid, ctx->nsm * occ));
+    ctx->l_eval = Launch{grid, sm};
+  }
+  ctx->l_a64 = make_launch(ctx, 6, smem_for(2, mx, A.tile_nnz, A.max_rows), A.ntiles);
+  ctx->l_t64 = make_launch(ctx, 6, smem_for(2, mx, T.tile_nnz, T.max_rows), T.ntiles);
+  ctx->restart_grid = std::max(1, std::min(ctx->nsm * 8, (std::max(ctx->m, ctx->n) + 255) / 256));
+  // reduction scratch: the largest grid plus split records, kEvalQ doubles each
+  const int gmax = std::max({ctx->l_eval.grid, ctx->l_a64.grid, ctx->l_t64.grid, 4096});
+  const int groups = std::max(A.ngroups, T.ngroups);
+  ctx->partials_len = (size_t)(gmax + groups + 1) * kEvalQ;
+  CKS(dalloc(ctx, &ctx->partials, ctx->partials_len));
+  CKS(dalloc(ctx, &ctx->split_q, (size_t)(T.ngroups + 1) * kEvalQ));
+  return PDHG_OK;
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
+  IterBuffers<T> B{};
+  B.a_rp = ctx->a_rp;
+  B.a_col = ctx->a_col;
+  B.t_rp = ctx->t_rp;
+  B.t_col = ctx->t_col;
+  if constexpr (sizeof(T) == 4) {
+    B.a_val = (const T*)ctx->a_val32;
+    B.t_val = (const T*)ctx->t_val32;
+    B.c_t = (const T*)ctx->c_t32;
+    B.b_t = (const T*)ctx->b_t32;
+  } else {
+    B.a_val = (const T*)ctx->a_val64;
+    B.t_val = (const T*)ctx->t_val64;
+    B.c_t = (const T*)ctx->c_t64;
+    B.b_t = (const T*)ctx->b_t64;
+  }
+  B.a_sched = ctx->sa.view;
+  B.t_sched = ctx->st.view;
+  B.x = (T*)ctx->x;
+  B.y = (T*)ctx->y;
+  B.x_avg = (T*)ctx->x_avg;
+  B.y_avg = (T*)ctx->y_avg;
+  B.x_last = (T*)ctx->x_last;
+  B.y_last = (T*)ctx->y_last;
+  B.Ax = (T*)ctx->Ax;
+  B.Ax_avg = (T*)ctx->Ax_avg;
+  B.c_t64 = ctx->c_t64;
+  B.b_t64 = ctx->b_t64;
+  B.D_r = ctx->D_r;
+  B.D_c = ctx->D_c;
+  B.sc = ctx->sc;
+  B.partials = ctx->partials;
+  B.split_q = ctx->split_q;
+  B.log_k = ctx->log_k;
+  B.log_flags = ctx->log_flags;
+  B.log_kkt = ctx->log_kkt;
+  B.m = ctx->m;
+  B.n = ctx->n;
+  return B;
+}
+
+// `len` iterations followed by the evaluation and the restart.  With
+// `timing`, events bracket the primal and dual kernels of iteration len/2.
+template <typename T>
+static void enqueue_chunk(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
+  const IterBuffers<T> B = iter_buffers<T>(ctx);
+  ctx->launches += 2LL * len + 2;
+  for (int i = 0; i < len; ++i) {
+    const bool sample = timing && i == len / 2;
+    if (sample) cudaEventRecordWithFlags(timing[0], ctx->stream, cudaEventRecordExternal);
+    launch_primal<T>(B, ctx->l_prim, i, ctx->stream);
+    if (sample) {
+      cudaEventRecordWithFlags(timing[1], ctx->stream, cudaEventRecordExternal);
+      cudaEventRecordWithFlags(timing[2], ctx->stream, cudaEventRecordExternal);
+    }
+    launch_dual<T>(B, ctx->l_dual, i, ctx->stream);
+    if (sample) cudaEventRecordWithFlags(timing[3], ctx->stream, cudaEventRecordExternal);
+  }
+  launch_eval<T>(B, ctx->l_eval, len, ctx->stream);
+  launch_restart<T>(B, ctx->restart_grid, ctx->stream);
+}
+
+static void enqueue_chunk_any(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
+  if (ctx->mixed)
+    enqueue_chunk<float>(ctx, len, timing);
+  else
+    enqueue_chunk<double>(ctx, len, timing);
+}
+
+static pdhg_status build_graphs(pdhg_ctx* ctx) {
+  const int F = ctx->opt.eval_freq;
+  for (int g = 0; g < 2; ++g) {
+    if (ctx->chunk_exec[g]) continue;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = ctx->launches;
+    enqueue_chunk_any(ctx, F, ctx->opt.kernel_timing ? ctx->ev_k[g] : nullptr);
+    ctx->launches = before;  // captured, not launched
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e != cudaSuccess) {
+      set_error("graph capture failed: %s", cudaGetErrorString(e));
+      return PDHG_CUDA_ERROR;
+    }
+    CK(cudaGraphInstantiate(&ctx->chunk_exec[g], graph, 0));
+    cudaGraphDestroy(graph);
+  }
+  return PDHG_OK;
+}
+
+static size_t elem(const pdhg_ctx* ctx) { return ctx->mixed ? sizeof(float) : sizeof(double); }
+
+// ---------------------------------------------------------------------------
+// create
+// ---------------------------------------------------------------------------
+extern "C" void pdhg_default_options(pdhg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = PDHG_FP64;
+  o->eval_freq = 64;
+  o->ruiz_iters = 10;
+  o->pock_chambolle = 1;
+  o->eta_safety = 0.95;
+  o->power_max_iter = 200;
+  o->power_rel_tol = 1e-10;
+  o->beta_sufficient = 0.2;
+  o->beta_necessary = 0.8;
+  o->beta_artificial = 0.36;
+  o->theta = 0.5;
+  o->io_on_device = 0;
+  o->stream = nullptr;
+  o->use_graphs = 1;
+  o->autotune = 1;
+  o->tile_nnz = 0;
+  o->kernel_timing = 0;
+  o->verbose = 0;
+}
+
+static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int32_t* col,
+                               const double* val, const double* b, const double* c) {
+  const int m = ctx->m, n = ctx->n;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev));
+  int optin = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  ctx->smem_optin = (size_t)optin;
+  if (ctx->opt.stream) {
+    ctx->stream = (cudaStream_t)ctx->opt.stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  CK(configure_tile_kernels(ctx->smem_optin));
+  CK(configure_setup_kernels(ctx->smem_optin));
+
+  // row pointer on the host (scheduler) and its checks
+  ctx->h_a_rp.resize((size_t)m + 1);
+  if (ctx->opt.io_on_device) {
+    CK(cudaMemcpyAsync(ctx->h_a_rp.data(), row_ptr, sizeof(int32_t) * (m + 1),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::memcpy(ctx->h_a_rp.data(), row_ptr, sizeof(int32_t) * (m + 1));
+  }
+  if (ctx->h_a_rp[0] != 0) {
+    set_error("row_ptr[0] must be 0");
+    return PDHG_INVALID_ARG;
+  }
+  for (int i = 0; i < m; ++i)
+    if (ctx->h_a_rp[i + 1] < ctx->h_a_rp[i]) {
+      set_error("row_ptr decreases at row %d", i);
+      return PDHG_INVALID_ARG;
+    }
+  ctx->nnz = ctx->h_a_rp[m];
+  ctx->nnz_pad = (ctx->nnz + 7) / 4 * 4 + 4;
+  const int64_t nnz = ctx->nnz, np = ctx->nnz_pad;
+
+  // device arrays
+  CKS(dalloc(ctx, &ctx->a_rp, (size_t)m + 1));
+  CKS(dalloc(ctx, &ctx->t_rp, (size_t)n + 1));
+  CKS(dalloc(ctx, &ctx->a_col, np));
+  CKS(dalloc(ctx, &ctx->t_col, np));
+  CKS(dalloc(ctx, &ctx->a_val_orig, np));
+  CKS(dalloc(ctx, &ctx->t_val_orig, np));
+  CKS(dalloc(ctx, &ctx->a_val64, np));
+  CKS(dalloc(ctx, &ctx->t_val64, np));
+  if (ctx->mixed) {
+    CKS(dalloc(ctx, &ctx->a_val32, np));
+    CKS(dalloc(ctx, &ctx->t_val32, np));
+    CKS(dalloc(ctx, &ctx->b_t32, m));
+    CKS(dalloc(ctx, &ctx->c_t32, n));
+  }
+  CKS(dalloc(ctx, &ctx->b, m));
+  CKS(dalloc(ctx, &ctx->c, n));
+  CKS(dalloc(ctx, &ctx->b_t64, m));
+  CKS(dalloc(ctx, &ctx->c_t64, n));
+  CKS(dalloc(ctx, &ctx->D_r, m));
+  CKS(dalloc(ctx, &ctx->D_c, n));
+  const size_t es = elem(ctx);
+  void** vecs_n[] = {&ctx->x, &ctx->x_avg, &ctx->x_last};
+  void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg};
+  for (void** p : vecs_n) CKS(dalloc(ctx, (char**)p, es * n));
+  for (void** p : vecs_m) CKS(dalloc(ctx, (char**)p, es * m));
+  CKS(dalloc(ctx, &ctx->xs64, n));
+  CKS(dalloc(ctx, &ctx->ys64, m));
+  CKS(dalloc(ctx, &ctx->out_n1, n));
+  CKS(dalloc(ctx, &ctx->out_n2, n));
+  CKS(dalloc(ctx, &ctx->out_m1, m));
+  CKS(dalloc(ctx, &ctx->report, 8));
+  CKS(dalloc(ctx, &ctx->sums, 8));
+  CKS(dalloc(ctx, &ctx->sc, 1));
+  CKS(dalloc(ctx, &ctx->ps, 1));
+  CKS(dalloc(ctx, &ctx->log_k, ctx->log_cap));
+  CKS(dalloc(ctx, &ctx->log_flags, ctx->log_cap));
+  CKS(dalloc(ctx, &ctx->log_kkt, 3 * (size_t)ctx->log_cap));
+  int32_t* flags = nullptr;
+  int32_t *cnt = nullptr, *tmp = nullptr;
+  CKS(dalloc(ctx, &flags, 1));
+  CKS(dalloc(ctx, &cnt, (size_t)n + 1));
+  CKS(dalloc(ctx, &tmp, (size_t)n / 1024 + 8));
+
+  CK(cudaMemsetAsync(ctx->a_col, 0, sizeof(int32_t) * np, ctx->stream));
+  CK(cudaMemsetAsync(ctx->t_col, 0, sizeof(int32_t) * np, ctx->stream));
+  CK(cudaMemsetAsync(ctx->a_val_orig, 0, sizeof(double) * np, ctx->stream));
+  CK(cudaMemsetAsync(ctx->t_val_orig, 0, sizeof(double) * np, ctx->stream));
+  CK(cudaMemsetAsync(ctx->a_val64, 0, sizeof(double) * np, ctx->stream));
+  CK(cudaMemsetAsync(ctx->t_val64, 0, sizeof(double) * np, ctx->stream));
+  if (ctx->mixed) {
+    CK(cudaMemsetAsync(ctx->a_val32, 0, sizeof(float) * np, ctx->stream));
+    CK(cudaMemsetAsync(ctx->t_val32, 0, sizeof(float) * np, ctx->stream));
+  }
+  CK(cudaMemcpyAsync(ctx->a_rp, ctx->h_a_rp.data(), sizeof(int32_t) * (m + 1),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CKS(copy_in(ctx, ctx->a_col, col, sizeof(int32_t) * nnz));
+  CKS(copy_in(ctx, ctx->a_val_orig, val, sizeof(double) * nnz));
+  CKS(copy_in(ctx, ctx->b, b, sizeof(double) * m));
+  CKS(copy_in(ctx, ctx->c, c, sizeof(double) * n));
+
+  // validation on device
+  CK(cudaMemsetAsync(flags, 0, sizeof(int32_t), ctx->stream));
+  launch_validate(m, n, ctx->a_rp, ctx->a_col, ctx->a_val_orig, ctx->b, ctx->c, flags, ctx->stream);
+  ctx->launches += 1;
+  int32_t hflags = 0;
+  CK(cudaMemcpyAsync(&hflags, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hflags) {
+    set_error("invalid LP data (flags 0x%x: 1 column out of range, 2 columns not strictly "
+              "increasing in a row, 4 non-finite A, 8 non-finite b, 16 non-finite c)",
+              hflags);
+    return PDHG_INVALID_ARG;
+  }
+
+  // a1: stable transpose A -> A^T (original values)
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), ctx->stream));
+  launch_col_hist(nnz, ctx->a_col, cnt, ctx->stream);
+  launch_scan(cnt, ctx->t_rp, n, tmp, ctx->stream);
+  CK(cudaMemcpyAsync(cnt, ctx->t_rp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  launch_scatter(m, ctx->a_rp, ctx->a_col, ctx->a_val_orig, cnt, ctx->t_col, ctx->t_val_orig,
+                 ctx->stream);
+  ctx->launches += 1 + (n > 0 ? 3 : 0) + 1;  // histogram, scan, scatter
+  ctx->h_t_rp.resize((size_t)n + 1);
+  CK(cudaMemcpyAsync(ctx->h_t_rp.data(), ctx->t_rp, sizeof(int32_t) * (n + 1),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  {
+    std::vector<int32_t> longs;
+    for (int j = 0; j < n; ++j)
+      if (ctx->h_t_rp[j + 1] - ctx->h_t_rp[j] > 32) longs.push_back(j);
+    int32_t* d_ids = nullptr;
+    int32_t* tk = nullptr;
+    double* tv = nullptr;
+    if (!longs.empty()) {
+      CKS(dalloc(ctx, &d_ids, longs.size()));
+      CKS(dalloc(ctx, &tk, np));
+      CKS(dalloc(ctx, &tv, np));
+      CK(cudaMemcpyAsync(d_ids, longs.data(), sizeof(int32_t) * longs.size(),
+                         cudaMemcpyHostToDevice, ctx->stream));
+    }
+    launch_segsort(n, ctx->t_rp, ctx->t_col, ctx->t_val_orig, d_ids, (int)longs.size(), tk, tv,
+                   ctx->stream);
+    ctx->launches += longs.empty() ? 1 : 2;
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  CK(cudaGetLastError());
+
+  // a2: Ruiz (infinity norm) then Pock-Chambolle (alpha = 1)
+  double *r = ctx->out_m1, *s = ctx->out_n1;
+  launch_fill(ctx->D_r, 1.0, m, ctx->stream);
+  launch_fill(ctx->D_c, 1.0, n, ctx->stream);
+  const int rounds = ctx->opt.ruiz_iters + (ctx->opt.pock_chambolle ? 1 : 0);
+  for (int it = 0; it < rounds; ++it) {
+    const int mode = it < ctx->opt.ruiz_iters ? 0 : 1;
+    launch_row_stat(m, ctx->a_rp, ctx->a_col, ctx->a_val_orig, ctx->D_r, ctx->D_c, mode, r,
+                    ctx->stream);
+    launch_row_stat(n, ctx->t_rp, ctx->t_col, ctx->t_val_orig, ctx->D_c, ctx->D_r, mode, s,
+                    ctx->stream);
+    launch_div(ctx->D_r, r, m, ctx->stream);
+    launch_div(ctx->D_c, s, n, ctx->stream);
+  }
+  launch_scale_vals(m, ctx->a_rp, ctx->a_col, ctx->a_val_orig, ctx->D_r, ctx->D_c, 0,
+                    ctx->a_val64, ctx->a_val32, ctx->stream);
+  launch_scale_vals(n, ctx->t_rp, ctx->t_col, ctx->t_val_orig, ctx->D_r, ctx->D_c, 1,
+                    ctx->t_val64, ctx->t_val32, ctx->stream);
+  launch_scale_vec(m, ctx->D_r, ctx->b, ctx->b_t64, ctx->b_t32, ctx->stream);
+  launch_scale_vec(n, ctx->D_c, ctx->c, ctx->c_t64, ctx->c_t32, ctx->stream);
+  ctx->launches += 2 + 4LL * rounds + 4;
+  CK(cudaGetLastError());
+
+  // zero state (also what the autotuner multiplies)
+  for (void** p : vecs_n) CK(cudaMemsetAsync(*p, 0, es * n, ctx->stream));
+  for (void** p : vecs_m) CK(cudaMemsetAsync(*p, 0, es * m, ctx->stream));
+
+  // tile schedules
+  CKS(choose_schedules(ctx));
+
+  // a3: power iteration on A~^T A~ (float64)
+  {
+    double *v = ctx->xs64, *u = ctx->ys64, *w = ctx->out_n2;
+    launch_pow_init(n, v, ctx->ps, ctx->opt.power_max_iter, ctx->opt.power_rel_tol, ctx->stream);
+    ctx->launches += 1;
+    for (int it = 0; it < ctx->opt.power_max_iter; ++it) {
+      launch_pow_Av(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64, v, u, ctx->ps, ctx->l_a64,
+                    ctx->stream);
+      launch_pow_ATu(ctx->st.view, ctx->t_rp, ctx->t_col, ctx->t_val64, u, v, w, ctx->partials,
+                     ctx->ps, ctx->l_t64, ctx->stream);
+      launch_pow_norm(n, w, v, ctx->ps, ctx->stream);
+      ctx->launches += 3;
+      if ((it & 15) == 15) {
+        PowerState hp;
+        CK(cudaMemcpyAsync(&hp, ctx->ps, sizeof(hp), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (hp.stopped) break;
+      }
+    }
+    CK(cudaGetLastError());
+  }
+
+  // norms, omega_0, tau, sigma, first restart point
+  {
+    Scalars h{};
+    h.eval_freq = ctx->opt.eval_freq;
+    h.beta_suff = ctx->opt.beta_sufficient;
+    h.beta_nec = ctx->opt.beta_necessary;
+    h.beta_art = ctx->opt.beta_artificial;
+    h.theta = ctx->opt.theta;
+    h.log_cap = ctx->log_cap;
+    h.status = PDHG_MAX_ITER;
+    CK(cudaMemcpyAsync(ctx->sc, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    const int g = 256;
+    const double* srcs[5] = {ctx->b, ctx->c, ctx->b_t64, ctx->c_t64, ctx->c_t64};
+    const int64_t lens[5] = {m, n, m, n, n};
+    const int modes[5] = {1, 1, 1, 1, 2};
+    for (int q = 0; q < 5; ++q) {
+      launch_dot_partials(lens[q], srcs[q], nullptr, modes[q], ctx->partials, g, ctx->stream);
+      launch_sum_final(ctx->partials, g, ctx->sums + q, ctx->stream);
+    }
+    launch_init_scalars(ctx->sc, ctx->sums, ctx->ps, ctx->opt.eta_safety, ctx->stream);
+    ctx->launches += 11;
+    Scalars hs;
+    PowerState hp;
+    CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&hp, ctx->ps, sizeof(hp), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->omega0 = hs.omega;
+    ctx->power_iters = hp.k;
+  }
+
+  // polling / timing resources
+  for (int g = 0; g < 2; ++g) {
+    CK(cudaEventCreateWithFlags(&ctx->ev_done[g], cudaEventDisableTiming));
+    CK(cudaMallocHost((void**)&ctx->h_sc[g], sizeof(Scalars)));
+    for (int e = 0; e < 4; ++e) CK(cudaEventCreate(&ctx->ev_k[g][e]));
+  }
+  CK(cudaGetLastError());
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const int32_t* row_ptr,
+                                   const int32_t* col, const double* val, const double* b,
+                                   const double* c, const pdhg_options* opt) {
+  g_last_error.clear();
+  if (!out) {
+    set_error("out is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (m < 1 || n < 1 || !row_ptr || !b || !c) {
+    set_error("need m >= 1, n >= 1 and non-NULL row_ptr, b, c");
+    return PDHG_INVALID_ARG;
+  }
+  pdhg_ctx* ctx = new (std::nothrow) pdhg_ctx();
+  if (!ctx) {
+    set_error("out of host memory");
+    return PDHG_OOM;
+  }
+  if (opt)
+    ctx->opt = *opt;
+  else
+    pdhg_default_options(&ctx->opt);
+  if (ctx->opt.eval_freq < 1 || ctx->opt.ruiz_iters < 0 || ctx->opt.power_max_iter < 0 ||
+      (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED) ||
+      ctx->opt.tile_nnz < 0 || ctx->opt.tile_nnz > 8192) {
+    set_error("invalid options (eval_freq >= 1, ruiz_iters >= 0, precision 0/1, "
+              "0 <= tile_nnz <= 8192)");
+    delete ctx;
+    return PDHG_INVALID_ARG;
+  }
+  ctx->m = m;
+  ctx->n = n;
+  ctx->mixed = ctx->opt.precision == PDHG_FP32_MIXED;
+  pdhg_status st = PDHG_OK;
+  if ((col == nullptr || val == nullptr) && row_ptr) {
+    // an all-zero A is legal only with nnz = 0; checked after row_ptr is read
+  }
+  st = create_impl(ctx, row_ptr, col, val, b, c);
+  if (st < 0) {
+    const std::string msg = g_last_error;
+    pdhg_destroy(ctx);
+    g_last_error = msg;
+    return st;
+  }
+  *out = ctx;
+  return PDHG_OK;
+}
+
+extern "C" void pdhg_destroy(pdhg_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (int g = 0; g < 2; ++g) {
+    if (ctx->chunk_exec[g]) cudaGraphExecDestroy(ctx->chunk_exec[g]);
+    if (ctx->ev_done[g]) cudaEventDestroy(ctx->ev_done[g]);
+    if (ctx->h_sc[g]) cudaFreeHost(ctx->h_sc[g]);
+    for (int e = 0; e < 4; ++e)
+      if (ctx->ev_k[g][e]) cudaEventDestroy(ctx->ev_k[g][e]);
+  }
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+extern "C" pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_iter) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  if (!(eps_rel >= 0.0) || max_iter < 0) {
+    set_error("need eps_rel >= 0 and max_iter >= 0");
+    return PDHG_INVALID_ARG;
+  }
+  ctx->report_valid = false;
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  long long k = hs.k;
+  if (k >= max_iter) {
+    ctx->last_status = PDHG_MAX_ITER;
+    return PDHG_MAX_ITER;
+  }
+  hs.eps = eps_rel;
+  hs.max_iter = max_iter;
+  hs.done = 0;
+  hs.status = PDHG_MAX_ITER;
+  hs.restart_pending = 0;
+  hs.ticket = 0;
+  CK(cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->opt.use_graphs) CKS(build_graphs(ctx));
+  ctx->timing_sum[0] = ctx->timing_sum[1] = 0.0;
+  ctx->timing_n = 0;
+
+  // Chunks are issued one ahead: after issuing chunk j the host waits for
+  // chunk j-1's status copy, so the GPU always has queued work.  A chunk
+  // issued after the device finished runs as no-op kernels.
+  const long long F = ctx->opt.eval_freq;
+  int slot = 0;
+  bool pending[2] = {false, false}, sampled[2] = {false, false}, stop = false;
+  long long expect_k[2] = {0, 0};
+  auto drain = [&](int sl) -> pdhg_status {
+    CK(cudaEventSynchronize(ctx->ev_done[sl]));
+    pending[sl] = false;
+    const Scalars* h = ctx->h_sc[sl];
+    if (sampled[sl] && h->k == expect_k[sl]) {
+      float a = 0.f, d = 0.f;
+      CK(cudaEventElapsedTime(&a, ctx->ev_k[sl][0], ctx->ev_k[sl][1]));
+      CK(cudaEventElapsedTime(&d, ctx->ev_k[sl][2], ctx->ev_k[sl][3]));
+      ctx->timing_sum[0] += a;
+      ctx->timing_sum[1] += d;
+      ctx->timing_n += 1;
+    }
+    sampled[sl] = false;
+    if (h->done) stop = true;
+    return PDHG_OK;
+  };
+  while (k < max_iter && !stop) {
+    const long long next = std::min<long long>((k / F + 1) * F, max_iter);
+    const int len = (int)(next - k);
+    if (len == F && ctx->opt.use_graphs) {
+      CK(cudaGraphLaunch(ctx->chunk_exec[slot], ctx->stream));
+      ctx->launches += 2 * F + 2;
+      sampled[slot] = ctx->opt.kernel_timing != 0;
+    } else {
+      enqueue_chunk_any(ctx, len, nullptr);
+      CK(cudaGetLastError());
+      sampled[slot] = false;
+    }
+    CK(cudaMemcpyAsync(ctx->h_sc[slot], ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaEventRecord(ctx->ev_done[slot], ctx->stream));
+    pending[slot] = true;
+    expect_k[slot] = next;
+    k = next;
+    const int other = slot ^ 1;
+    if (pending[other]) CKS(drain(other));
+    slot = other;
+  }
+  for (int i = 0; i < 2; ++i) {
+    const int sl = slot ^ 1 ^ i;  // the older pending chunk first
+    if (pending[sl]) CKS(drain(sl));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  CK(cudaMemcpy(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost));
+  ctx->last_status = hs.done ? hs.status : PDHG_MAX_ITER;
+  if (!hs.done && hs.k >= max_iter) ctx->last_status = PDHG_MAX_ITER;
+  return (pdhg_status)ctx->last_status;
+}
+
+// ---------------------------------------------------------------------------
+// report of the returned iterate (float64, original model)
+// ---------------------------------------------------------------------------
+static pdhg_status returned_iterate64(pdhg_ctx* ctx, const double** xs, const double** ys) {
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const bool avg = hs.done && hs.status == PDHG_OK && hs.chosen_avg;
+  void* xsrc = avg ? ctx->x_avg : ctx->x;
+  void* ysrc = avg ? ctx->y_avg : ctx->y;
+  if (ctx->mixed) {
+    launch_convert_f2d((const float*)xsrc, ctx->xs64, ctx->n, ctx->stream);
+    launch_convert_f2d((const float*)ysrc, ctx->ys64, ctx->m, ctx->stream);
+    ctx->launches += 2;
+    *xs = ctx->xs64;
+    *ys = ctx->ys64;
+  } else {
+    *xs = (const double*)xsrc;
+    *ys = (const double*)ysrc;
+  }
+  return PDHG_OK;
+}
+
+static pdhg_status compute_report(pdhg_ctx* ctx) {
+  const double *xs, *ys;
+  CKS(returned_iterate64(ctx, &xs, &ys));
+  double* pn = ctx->partials;
+  const int gn = ctx->l_t64.grid + ctx->st.view.ngroups;
+  double* pm = ctx->partials + 4 * (size_t)(gn + 1);
+  const int gm = ctx->l_a64.grid + ctx->sa.view.ngroups;
+  launch_report_n(ctx->st.view, ctx->t_rp, ctx->t_col, ctx->t_val64, xs, ys, ctx->c_t64, ctx->D_c,
+                  ctx->out_n1, ctx->out_n2, pn, ctx->l_t64, ctx->stream);
+  launch_report_m(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64, xs, ys, ctx->b_t64, ctx->D_r,
+                  ctx->out_m1, pm, ctx->l_a64, ctx->stream);
+  launch_report_final(pn, gn, pm, gm, ctx->report, ctx->stream);
+  ctx->launches += 3;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->report_h, ctx->report, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->report_valid = true;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get(pdhg_ctx* ctx, double* x, double* y, double* z, double* r_P,
+                                double* r_D, double* gap) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  CKS(compute_report(ctx));
+  CKS(copy_out(ctx, x, ctx->out_n1, sizeof(double) * ctx->n));
+  CKS(copy_out(ctx, z, ctx->out_n2, sizeof(double) * ctx->n));
+  CKS(copy_out(ctx, y, ctx->out_m1, sizeof(double) * ctx->m));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (r_P) *r_P = ctx->report_h[0];
+  if (r_D) *r_D = ctx->report_h[1];
+  if (gap) *gap = ctx->report_h[2];
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_info(pdhg_ctx* ctx, int64_t* iters, int64_t* restarts,
+                                     double* max_violation, int32_t* chosen_average,
+                                     int32_t* last_status) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (iters) *iters = hs.k;
+  if (restarts) *restarts = hs.restarts;
+  if (chosen_average) *chosen_average = (hs.done && hs.status == PDHG_OK) ? hs.chosen_avg : 0;
+  if (last_status) *last_status = ctx->last_status;
+  if (max_violation) {
+    if (!ctx->report_valid) CKS(compute_report(ctx));
+    *max_violation = ctx->report_h[3];
+  }
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_warmstart_point(pdhg_ctx* ctx, double mu_min, double delta_max,
+                                            double alpha_min, int32_t unscaled, double* x_ws,
+                                            double* y_ws, double* z_ws, double* mu_target) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  if (!(mu_min > 0.0) || !(delta_max >= 0.0) || !(alpha_min > 0.0)) {
+    set_error("need mu_min > 0, delta_max >= 0, alpha_min > 0");
+    return PDHG_INVALID_ARG;
+  }
+  const double *xs, *ys;
+  CKS(returned_iterate64(ctx, &xs, &ys));
+  double* zs = ctx->out_n2;
+  double* mu = ctx->report + 7;
+  launch_ws_z(ctx->st.view, ctx->t_rp, ctx->t_col, ctx->t_val64, xs, ys, ctx->c_t64, zs,
+              ctx->partials, ctx->l_t64, ctx->stream);
+  launch_ws_mu(ctx->partials, ctx->l_t64.grid + ctx->st.view.ngroups, ctx->n, mu_min, mu,
+               ctx->stream);
+  // outputs land in out_n1 (x'), out_m1 (y), and z' overwrites z~ in place
+  launch_ws_apply(ctx->n, ctx->m, xs, zs, ys, mu, delta_max, alpha_min, unscaled, ctx->D_r,
+                  ctx->D_c, ctx->out_n1, ctx->out_m1, zs, ctx->stream);
+  ctx->launches += 3;
+  CK(cudaGetLastError());
+  CKS(copy_out(ctx, x_ws, ctx->out_n1, sizeof(double) * ctx->n));
+  CKS(copy_out(ctx, y_ws, ctx->out_m1, sizeof(double) * ctx->m));
+  CKS(copy_out(ctx, z_ws, zs, sizeof(double) * ctx->n));
+  double hmu = 0;
+  CK(cudaMemcpyAsync(&hmu, mu, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (mu_target) *mu_target = hmu;
+  ctx->report_valid = false;  // report buffers were reused
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_scaling(pdhg_ctx* ctx, double* D_r, double* D_c,
+                                        double* sigma_max, double* eta, double* omega0,
+                                        int32_t* power_iters) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  CKS(copy_out(ctx, D_r, ctx->D_r, sizeof(double) * ctx->m));
+  CKS(copy_out(ctx, D_c, ctx->D_c, sizeof(double) * ctx->n));
+  PowerState hp;
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hp, ctx->ps, sizeof(hp), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (sigma_max) *sigma_max = std::sqrt(std::max(hp.lam, 0.0));
+  if (eta) *eta = hs.eta;
+  if (omega0) *omega0 = ctx->omega0;
+  if (power_iters) *power_iters = hp.k;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_transpose(pdhg_ctx* ctx, int32_t* row_ptr_t, int32_t* col_t,
+                                          double* val_t) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  CKS(copy_out(ctx, row_ptr_t, ctx->t_rp, sizeof(int32_t) * ((size_t)ctx->n + 1)));
+  CKS(copy_out(ctx, col_t, ctx->t_col, sizeof(int32_t) * ctx->nnz));
+  CKS(copy_out(ctx, val_t, ctx->t_val_orig, sizeof(double) * ctx->nnz));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+// float64 host/device buffer <-> iterate buffer in the iteration precision
+static pdhg_status state_out(pdhg_ctx* ctx, double* dst, const void* src, int len) {
+  if (!dst) return PDHG_OK;
+  if (ctx->mixed) {
+    double* tmp = len == ctx->n ? ctx->xs64 : ctx->ys64;
+    launch_convert_f2d((const float*)src, tmp, len, ctx->stream);
+    return copy_out(ctx, dst, tmp, sizeof(double) * len);
+  }
+  return copy_out(ctx, dst, src, sizeof(double) * len);
+}
+static pdhg_status state_in(pdhg_ctx* ctx, void* dst, const double* src, int len) {
+  if (!src) return PDHG_OK;
+  if (ctx->mixed) {
+    double* tmp = len == ctx->n ? ctx->xs64 : ctx->ys64;
+    CKS(copy_in(ctx, tmp, src, sizeof(double) * len));
+    launch_convert_d2f(tmp, (float*)dst, len, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDHG_OK;
+  }
+  return copy_in(ctx, dst, src, sizeof(double) * len);
+}
+
+extern "C" pdhg_status pdhg_get_state(pdhg_ctx* ctx, double* x, double* y, double* x_avg,
+                                      double* y_avg, double* x_last, double* y_last,
+                                      double* scalars) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  const int n = ctx->n, m = ctx->m;
+  CKS(state_out(ctx, x, ctx->x, n));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CKS(state_out(ctx, x_avg, ctx->x_avg, n));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CKS(state_out(ctx, x_last, ctx->x_last, n));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CKS(state_out(ctx, y, ctx->y, m));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CKS(state_out(ctx, y_avg, ctx->y_avg, m));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CKS(state_out(ctx, y_last, ctx->y_last, m));
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (scalars) {
+    scalars[0] = hs.omega;
+    scalars[1] = (double)hs.k;
+    scalars[2] = (double)hs.t;
+    scalars[3] = (double)hs.restarts;
+    scalars[4] = hs.kkt_last;
+    scalars[5] = hs.kkt_prev;
+    scalars[6] = hs.eta;
+    scalars[7] = 0.0;
+  }
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const double* y,
+                                      const double* x_avg, const double* y_avg,
+                                      const double* x_last, const double* y_last,
+                                      const double* scalars) {
+  g_last_error.clear();
+  if (!ctx || !x || !y || !x_avg || !y_avg || !x_last || !y_last || !scalars) {
+    set_error("pdhg_set_state needs every argument");
+    return PDHG_INVALID_ARG;
+  }
+  const int n = ctx->n, m = ctx->m;
+  CKS(state_in(ctx, ctx->x, x, n));
+  CKS(state_in(ctx, ctx->x_avg, x_avg, n));
+  CKS(state_in(ctx, ctx->x_last, x_last, n));
+  CKS(state_in(ctx, ctx->y, y, m));
+  CKS(state_in(ctx, ctx->y_avg, y_avg, m));
+  CKS(state_in(ctx, ctx->y_last, y_last, m));
+  // caches A~x and A~x_avg in the iteration precision
+  const size_t smem = smem_for(0, ctx->mixed, ctx->sa.view.tile_nnz, ctx->sa.view.max_rows);
+  if (ctx->mixed) {
+    launch_spmv<float>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val32, (const float*)ctx->x,
+                       (float*)ctx->Ax, ctx->l_dual, ctx->stream);
+    launch_spmv<float>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val32,
+                       (const float*)ctx->x_avg, (float*)ctx->Ax_avg, ctx->l_dual, ctx->stream);
+  } else {
+    launch_spmv<double>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64, (const double*)ctx->x,
+                        (double*)ctx->Ax, ctx->l_dual, ctx->stream);
+    launch_spmv<double>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64,
+                        (const double*)ctx->x_avg, (double*)ctx->Ax_avg, ctx->l_dual, ctx->stream);
+  }
+  (void)smem;
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  hs.omega = scalars[0];
+  hs.k = (long long)scalars[1];
+  hs.t = (long long)scalars[2];
+  hs.restarts = (long long)scalars[3];
+  hs.kkt_last = scalars[4];
+  hs.kkt_prev = scalars[5];
+  hs.tau = hs.eta / hs.omega;
+  hs.sigma = hs.eta * hs.omega;
+  hs.done = 0;
+  hs.restart_pending = 0;
+  hs.ticket = 0;
+  CK(cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  ctx->report_valid = false;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_log(pdhg_ctx* ctx, int32_t cap, int32_t* count, int64_t* k,
+                                    int32_t* flags, double* kkt) {
+  g_last_error.clear();
+  if (!ctx || cap < 0) {
+    set_error("ctx is NULL or cap < 0");
+    return PDHG_INVALID_ARG;
+  }
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int cnt = std::min(cap, hs.log_count);
+  if (count) *count = hs.log_count;
+  if (cnt > 0) {
+    if (k) CK(cudaMemcpy(k, ctx->log_k, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost));
+    if (flags) CK(cudaMemcpy(flags, ctx->log_flags, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost));
+    if (kkt) CK(cudaMemcpy(kkt, ctx->log_kkt, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost));
+  }
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_kernel_timing(pdhg_ctx* ctx, double* primal_ms, double* dual_ms,
+                                              int64_t* samples) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  const double nn = ctx->timing_n > 0 ? (double)ctx->timing_n : 1.0;
+  if (primal_ms) *primal_ms = ctx->timing_sum[0] / nn;
+  if (dual_ms) *dual_ms = ctx->timing_sum[1] / nn;
+  if (samples) *samples = ctx->timing_n;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int32_t* a_block,
+                                         int32_t* a_tiles, int32_t* at_tile_nnz,
+                                         int32_t* at_block, int32_t* at_tiles) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  if (a_tile_nnz) *a_tile_nnz = ctx->sa.view.tile_nnz;
+  if (a_block) *a_block = kBlock;
+  if (a_tiles) *a_tiles = ctx->sa.view.ntiles;
+  if (at_tile_nnz) *at_tile_nnz = ctx->st.view.tile_nnz;
+  if (at_block) *at_block = kBlock;
+  if (at_tiles) *at_tiles = ctx->st.view.ntiles;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_launch_count(pdhg_ctx* ctx, int64_t* launches) {
+  g_last_error.clear();
+  if (!ctx || !launches) {
+    set_error("ctx or launches is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  *launches = ctx->launches;
+  return PDHG_OK;
+}

@@ -1,0 +1,311 @@
+"""Python binding of libpdhg.so (argument marshalling only).
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts numpy arrays / torch tensors to pointers and back.  If the library
+is missing it raises: there is no CPU fallback.
+
+Host arrays (numpy, or CPU tensors) are copied by the library; CUDA tensors
+may be passed when the solver is created with ``device_io=True``, in which
+case every array argument and output is a device tensor on ``stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "_lib", "libpdhg.so")
+
+PDHG_OK = 0
+PDHG_CONVERGED = 0
+PDHG_MAX_ITER = 1
+PDHG_NUMERICAL_ERROR = 2
+PDHG_TIMEOUT = 3
+PDHG_INVALID_ARG = -1
+PDHG_CUDA_ERROR = -2
+PDHG_OOM = -3
+FP64, FP32_MIXED = 0, 1
+STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "numerical_error", 3: "timeout",
+                -1: "invalid_arg", -2: "cuda_error", -3: "oom"}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("eval_freq", ctypes.c_int32),
+        ("ruiz_iters", ctypes.c_int32),
+        ("pock_chambolle", ctypes.c_int32),
+        ("eta_safety", ctypes.c_double),
+        ("power_max_iter", ctypes.c_int32),
+        ("power_rel_tol", ctypes.c_double),
+        ("beta_sufficient", ctypes.c_double),
+        ("beta_necessary", ctypes.c_double),
+        ("beta_artificial", ctypes.c_double),
+        ("theta", ctypes.c_double),
+        ("io_on_device", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("use_graphs", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
+        ("tile_nnz", ctypes.c_int32),
+        ("kernel_timing", ctypes.c_int32),
+        ("verbose", ctypes.c_int32),
+    ]
+
+
+class PDHGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "pdhg_default_options": (None, [ctypes.POINTER(Options)]),
+    "pdhg_create": (_I32, [_PP, _I32, _I32, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
+    "pdhg_solve": (_I32, [_P, _D, _I64]),
+    "pdhg_get": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+    "pdhg_get_info": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "pdhg_warmstart_point": (_I32, [_P, _D, _D, _D, _I32, _P, _P, _P, _P]),
+    "pdhg_get_scaling": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+    "pdhg_get_transpose": (_I32, [_P, _P, _P, _P]),
+    "pdhg_get_state": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "pdhg_set_state": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "pdhg_get_log": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    "pdhg_get_kernel_timing": (_I32, [_P, _P, _P, _P]),
+    "pdhg_get_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+    "pdhg_get_launch_count": (_I32, [_P, _P]),
+    "pdhg_destroy": (None, [_P]),
+    "pdhg_last_error": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+
+
+def declared_symbols():
+    """Entry points this binding expects the library to export."""
+    return list(_SIGS)
+
+
+def lib(path: Optional[str] = None):
+    """Load libpdhg.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or LIBPATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} not found: build it with paper_2603_03150_gb300.build.build()")
+    L = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name, None)
+        if f is None:
+            continue  # optional entry points are checked by callers
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _LIB = L
+    return L
+
+
+def _check(status: int, allow_positive: bool = True) -> int:
+    if status < 0 or (not allow_positive and status != 0):
+        raise PDHGError(status, lib().pdhg_last_error().decode(errors="replace"))
+    return status
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """Pointer to a contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        assert a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _out_ptr(x, dtype=ctypes.c_double):
+    return ctypes.byref(x)
+
+
+class Solver:
+    """One LP  min c^T x, Ax = b, x >= 0  held by a library context.
+
+    ``row_ptr``/``col`` int32, ``val``/``b``/``c`` float64.  With
+    ``device_io=True`` they (and every output) are CUDA tensors."""
+
+    def __init__(self, m, n, row_ptr, col, val, b, c, precision: str = "fp64",
+                 eval_freq: int = 64, ruiz_iters: int = 10, pock_chambolle: bool = True,
+                 eta_safety: float = 0.95, power_max_iter: int = 200,
+                 power_rel_tol: float = 1e-10, device_io: bool = False, stream=None,
+                 use_graphs: bool = True, autotune: bool = True, tile_nnz: int = 0,
+                 kernel_timing: bool = False):
+        L = lib()
+        o = Options()
+        L.pdhg_default_options(ctypes.byref(o))
+        o.precision = FP32_MIXED if precision in ("fp32", "fp32_mixed", "mixed") else FP64
+        o.eval_freq = eval_freq
+        o.ruiz_iters = ruiz_iters
+        o.pock_chambolle = 1 if pock_chambolle else 0
+        o.eta_safety = eta_safety
+        o.power_max_iter = power_max_iter
+        o.power_rel_tol = power_rel_tol
+        o.io_on_device = 1 if device_io else 0
+        o.stream = stream
+        o.use_graphs = 1 if use_graphs else 0
+        o.autotune = 1 if autotune else 0
+        o.tile_nnz = tile_nnz
+        o.kernel_timing = 1 if kernel_timing else 0
+        self.m, self.n = int(m), int(n)
+        self.device_io = device_io
+        self.mixed = o.precision == FP32_MIXED
+        if not device_io:
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            c = np.ascontiguousarray(c, dtype=np.float64)
+        self._ctx = ctypes.c_void_p()
+        self._L = L
+        st = L.pdhg_create(ctypes.byref(self._ctx), self.m, self.n, _ptr(row_ptr), _ptr(col),
+                           _ptr(val), _ptr(b), _ptr(c), ctypes.byref(o))
+        _check(st, allow_positive=False)
+        self.status = None
+
+    @classmethod
+    def from_lp(cls, lp, **kw):
+        return cls(lp.m, lp.n, lp.row_ptr, lp.col, lp.val, lp.b, lp.c, **kw)
+
+    # ------------------------------------------------------------------
+    def _new(self, length):
+        if self.device_io:
+            import torch
+            return torch.empty(length, dtype=torch.float64, device="cuda")
+        return np.empty(length, dtype=np.float64)
+
+    def solve(self, eps_rel: float = 1e-4, max_iter: int = 1_000_000) -> int:
+        self.status = _check(self._L.pdhg_solve(self._ctx, eps_rel, max_iter))
+        return self.status
+
+    def get(self):
+        x, y, z = self._new(self.n), self._new(self.m), self._new(self.n)
+        rp, rd, gap = _D(), _D(), _D()
+        _check(self._L.pdhg_get(self._ctx, _ptr(x), _ptr(y), _ptr(z), ctypes.byref(rp),
+                                ctypes.byref(rd), ctypes.byref(gap)))
+        return dict(x=x, y=y, z=z, r_P=rp.value, r_D=rd.value, gap=gap.value)
+
+    def info(self):
+        it, rs, mv, ca, ls = _I64(), _I64(), _D(), _I32(), _I32()
+        _check(self._L.pdhg_get_info(self._ctx, ctypes.byref(it), ctypes.byref(rs),
+                                     ctypes.byref(mv), ctypes.byref(ca), ctypes.byref(ls)))
+        return dict(iters=it.value, restarts=rs.value, max_violation=mv.value,
+                    chosen_average=bool(ca.value), status=ls.value)
+
+    def warmstart_point(self, mu_min: float = 1e-6, delta_max: float = 1e-4,
+                        alpha_min: float = 1e-6, unscaled: bool = False):
+        x, y, z = self._new(self.n), self._new(self.m), self._new(self.n)
+        mu = _D()
+        _check(self._L.pdhg_warmstart_point(self._ctx, mu_min, delta_max, alpha_min,
+                                            1 if unscaled else 0, _ptr(x), _ptr(y), _ptr(z),
+                                            ctypes.byref(mu)))
+        return x, y, z, mu.value
+
+    def scaling(self):
+        Dr, Dc = self._new(self.m), self._new(self.n)
+        smax, eta, om, pit = _D(), _D(), _D(), _I32()
+        _check(self._L.pdhg_get_scaling(self._ctx, _ptr(Dr), _ptr(Dc), ctypes.byref(smax),
+                                        ctypes.byref(eta), ctypes.byref(om), ctypes.byref(pit)))
+        return dict(D_r=Dr, D_c=Dc, sigma_max=smax.value, eta=eta.value, omega0=om.value,
+                    power_iters=pit.value)
+
+    def transpose(self, nnz: int):
+        rp = np.empty(self.n + 1, dtype=np.int32)
+        ci = np.empty(nnz, dtype=np.int32)
+        v = np.empty(nnz, dtype=np.float64)
+        if self.device_io:
+            import torch
+            rp, ci, v = (torch.from_numpy(a).cuda() for a in (rp, ci, v))
+        _check(self._L.pdhg_get_transpose(self._ctx, _ptr(rp), _ptr(ci), _ptr(v)))
+        return rp, ci, v
+
+    def state(self):
+        n, m = self.n, self.m
+        arrs = [self._new(n), self._new(m), self._new(n), self._new(m), self._new(n), self._new(m)]
+        sc = np.empty(8, dtype=np.float64)
+        _check(self._L.pdhg_get_state(self._ctx, *[_ptr(a) for a in arrs], _ptr(sc)))
+        keys = ["x", "y", "x_avg", "y_avg", "x_last", "y_last"]
+        d = dict(zip(keys, arrs))
+        d.update(omega=sc[0], k=int(sc[1]), t=int(sc[2]), restarts=int(sc[3]),
+                 kkt_last=sc[4], kkt_prev=sc[5], eta=sc[6])
+        return d
+
+    def set_state(self, st):
+        sc = np.array([st["omega"], st["k"], st["t"], st["restarts"], st["kkt_last"],
+                       st["kkt_prev"], st.get("eta", 0.0), 0.0], dtype=np.float64)
+        arrs = [st[k] for k in ["x", "y", "x_avg", "y_avg", "x_last", "y_last"]]
+        if not self.device_io:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        _check(self._L.pdhg_set_state(self._ctx, *[_ptr(a) for a in arrs], _ptr(sc)),
+               allow_positive=False)
+
+    def log(self, cap: int = 4096):
+        cnt = _I32()
+        k = np.zeros(cap, dtype=np.int64)
+        fl = np.zeros(cap, dtype=np.int32)
+        kk = np.zeros(3 * cap, dtype=np.float64)
+        _check(self._L.pdhg_get_log(self._ctx, cap, ctypes.byref(cnt), _ptr(k), _ptr(fl), _ptr(kk)))
+        c = min(cnt.value, cap)
+        out = []
+        for i in range(c):
+            f = int(fl[i])
+            out.append(dict(k=int(k[i]), restart=bool(f & 1),
+                            cand="average" if f & 2 else "current", r1=bool(f & 4),
+                            r2=bool(f & 8), r3=bool(f & 16), kkt_cur=kk[3 * i],
+                            kkt_avg=kk[3 * i + 1], omega=kk[3 * i + 2]))
+        return out
+
+    def kernel_timing(self):
+        a, d, s = _D(), _D(), _I64()
+        _check(self._L.pdhg_get_kernel_timing(self._ctx, ctypes.byref(a), ctypes.byref(d),
+                                              ctypes.byref(s)))
+        return dict(primal_ms=a.value, dual_ms=d.value, samples=s.value)
+
+    def schedule(self):
+        v = [_I32() for _ in range(6)]
+        _check(self._L.pdhg_get_schedule(self._ctx, *[ctypes.byref(x) for x in v]))
+        keys = ["a_tile_nnz", "a_block", "a_tiles", "at_tile_nnz", "at_block", "at_tiles"]
+        return {k: x.value for k, x in zip(keys, v)}
+
+    def launch_count(self) -> int:
+        v = _I64()
+        _check(self._L.pdhg_get_launch_count(self._ctx, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._L.pdhg_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
