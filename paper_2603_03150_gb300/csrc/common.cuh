@@ -19,8 +19,7 @@ struct Tile {
   int32_t nz_begin, nz_end;    // nonzeros [nz_begin, nz_end)
   int32_t split;               // -1: whole rows; else split-group index
   int32_t part;                // chunk index within the split group
-  int32_t lanes;               // threads per row in the reduction (power of 2)
-  int32_t pad;
+  int32_t pad0, pad1;
 };
 
 struct SplitGroup {
@@ -36,9 +35,11 @@ struct SchedView {
   int32_t* counters;  // [ngroups], zero between launches
   void* slots;        // [total parts * NV] partial sums
   int32_t ntiles;
-  int32_t tile_nnz;
-  int32_t max_rows;
+  int32_t tile_nnz;  // nonzero capacity of a tile (block * e - 4)
+  int32_t max_rows;  // rows per tile at most
   int32_t ngroups;   // split groups (records appended after block partials)
+  int32_t e;         // nonzeros per thread (4, 8 or 16)
+  int32_t pad;
 };
 
 // ---------------------------------------------------------------------------

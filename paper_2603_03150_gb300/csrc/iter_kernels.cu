@@ -26,14 +26,14 @@ struct PrimalEpi {
   }
 };
 
-template <typename T, int BLOCK>
+template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_primal(IterBuffers<T> B, int i) {
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const long long tt = B.sc->t + i;  // iterations since restart before this one
   PrimalEpi<T> epi{B.x, B.c_t, B.x_avg, (T)B.sc->tau, (T)(1.0 / (double)(tt + 1)), tt == 0};
   Gather<T, 1> g{{B.y}};
-  run_tiles<T, 1, BLOCK>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
+  run_tiles<T, 1, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -59,7 +59,7 @@ struct DualEpi {
   }
 };
 
-template <typename T, int BLOCK>
+template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_dual(IterBuffers<T> B, int i) {
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(BLOCK) k_dual(IterBuffers<T> B, int i) {
   DualEpi<T> epi{B.y,   B.b_t, B.Ax, B.y_avg, B.Ax_avg, (T)B.sc->sigma, (T)(1.0 / (double)(tt + 1)),
                  tt == 0};
   Gather<T, 1> g{{B.x}};
-  run_tiles<T, 1, BLOCK>(B.a_sched, B.a_rp, B.a_col, B.a_val, g, epi, smem);
+  run_tiles<T, 1, BLOCK, E>(B.a_sched, B.a_rp, B.a_col, B.a_val, g, epi, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -204,7 +204,7 @@ __device__ void eval_finalize(const IterBuffers<T>& B, const double* tot, int ch
   }
 }
 
-template <typename T, int BLOCK>
+template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
 #pragma unroll
     for (int k = 0; k < Q_N; ++k) epi.q[c][k] = 0.0;
   Gather<T, 2> g{{B.y, B.y_avg}};
-  run_tiles<T, 2, BLOCK>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
+  run_tiles<T, 2, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
   // m side: primal residual, dual objective, distance to the last restart point
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < B.m; i += gridDim.x * BLOCK) {
     const double bi = B.b_t64[i], dr = B.D_r[i], yl = (double)B.y_last[i];
@@ -289,17 +289,34 @@ __global__ void k_restart(IterBuffers<T> B) {
   }
 }
 
+// nonzeros per thread of a schedule -> template instantiation
+#define PDHG_DISPATCH_E(e, ...)                 \
+  switch (e) {                                  \
+    case 4: {                                   \
+      constexpr int E_ = 4;                     \
+      __VA_ARGS__;                              \
+    } break;                                    \
+    case 16: {                                  \
+      constexpr int E_ = 16;                    \
+      __VA_ARGS__;                              \
+    } break;                                    \
+    default: {                                  \
+      constexpr int E_ = 8;                     \
+      __VA_ARGS__;                              \
+    } break;                                    \
+  }
+
 template <typename T>
 void launch_primal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s) {
-  k_primal<T, kBlock><<<L.grid, kBlock, L.smem, s>>>(B, i);
+  PDHG_DISPATCH_E(B.t_sched.e, k_primal<T, kBlock, E_><<<L.grid, kBlock, L.smem, s>>>(B, i));
 }
 template <typename T>
 void launch_dual(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s) {
-  k_dual<T, kBlock><<<L.grid, kBlock, L.smem, s>>>(B, i);
+  PDHG_DISPATCH_E(B.a_sched.e, k_dual<T, kBlock, E_><<<L.grid, kBlock, L.smem, s>>>(B, i));
 }
 template <typename T>
 void launch_eval(const IterBuffers<T>& B, const Launch& L, int chunk, cudaStream_t s) {
-  k_eval<T, kBlock><<<L.grid, kBlock, L.smem, s>>>(B, chunk);
+  PDHG_DISPATCH_E(B.t_sched.e, k_eval<T, kBlock, E_><<<L.grid, kBlock, L.smem, s>>>(B, chunk));
 }
 template <typename T>
 void launch_restart(const IterBuffers<T>& B, int grid, cudaStream_t s) {
@@ -315,19 +332,19 @@ struct StoreEpi {
   __device__ __forceinline__ void row(int r, const T (&s)[1], int) { out[r] = s[0]; }
 };
 
-template <typename T, int BLOCK>
+template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_spmv(SchedView S, const int32_t* rp, const int32_t* col,
                                                const T* val, const T* v, T* out) {
   extern __shared__ __align__(16) unsigned char smem[];
   StoreEpi<T> epi{out};
   Gather<T, 1> g{{v}};
-  run_tiles<T, 1, BLOCK>(S, rp, col, val, g, epi, smem);
+  run_tiles<T, 1, BLOCK, E>(S, rp, col, val, g, epi, smem);
 }
 
 template <typename T>
 void launch_spmv(const SchedView& S, const int32_t* rp, const int32_t* col, const T* val,
                  const T* v, T* out, const Launch& L, cudaStream_t s) {
-  k_spmv<T, kBlock><<<L.grid, kBlock, L.smem, s>>>(S, rp, col, val, v, out);
+  PDHG_DISPATCH_E(S.e, k_spmv<T, kBlock, E_><<<L.grid, kBlock, L.smem, s>>>(S, rp, col, val, v, out));
 }
 
 // ---------------------------------------------------------------------------
@@ -370,7 +387,7 @@ __global__ void __launch_bounds__(BLOCK) k_report_n(SchedView S, const int32_t* 
   double* split_q = partials + 4 * (size_t)gridDim.x;
   ReportNEpi epi{x_s, c_t, D_c, x_out, z_out, 0.0, 0.0, 0.0, 0.0, split_q};
   Gather<double, 1> g{{y_s}};
-  run_tiles<double, 1, BLOCK>(S, rp, col, val, g, epi, smem);
+  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
   // infinity norm through a max-reduction, sums through block_sum
   const double v[3] = {epi.u2, epi.s3, epi.xz};
   double o[3];
@@ -422,7 +439,7 @@ __global__ void __launch_bounds__(BLOCK) k_report_m(SchedView S, const int32_t* 
   double* split_q = partials + 4 * (size_t)gridDim.x;
   ReportMEpi epi{y_s, b_t, D_r, y_out, 0.0, 0.0, 0.0, split_q};
   Gather<double, 1> g{{x_s}};
-  run_tiles<double, 1, BLOCK>(S, rp, col, val, g, epi, smem);
+  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
   const double v[2] = {epi.u1, epi.s4};
   double o[2];
   block_sum<BLOCK, 2>(v, o, red);
@@ -511,7 +528,7 @@ __global__ void __launch_bounds__(BLOCK) k_ws_z(SchedView S, const int32_t* rp, 
   __shared__ double red[BLOCK / 32];
   WsEpi epi{x_s, c_t, z_s, 0.0, partials + gridDim.x};
   Gather<double, 1> g{{y_s}};
-  run_tiles<double, 1, BLOCK>(S, rp, col, val, g, epi, smem);
+  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
   const double v[1] = {epi.xz};
   double o[1];
   block_sum<BLOCK, 1>(v, o, red);
@@ -608,50 +625,73 @@ PDHG_INST(float)
 PDHG_INST(double)
 #undef PDHG_INST
 
-// shared memory of the tile kernels: one helper per instantiation
-size_t tile_smem_1f(int tn, int mr) { return tile_smem_bytes<float, 1, kBlock>(tn, mr); }
-size_t tile_smem_1d(int tn, int mr) { return tile_smem_bytes<double, 1, kBlock>(tn, mr); }
-size_t tile_smem_2f(int tn, int mr) { return tile_smem_bytes<float, 2, kBlock>(tn, mr); }
-size_t tile_smem_2d(int tn, int mr) { return tile_smem_bytes<double, 2, kBlock>(tn, mr); }
+// shared memory of the tile kernels (NV vectors, precision, rows per tile)
+size_t tile_smem(int nv, bool f32, int max_rows) {
+  if (nv == 1) return f32 ? tile_smem_bytes<float, 1, kBlock>(max_rows)
+                          : tile_smem_bytes<double, 1, kBlock>(max_rows);
+  return f32 ? tile_smem_bytes<float, 2, kBlock>(max_rows) : tile_smem_bytes<double, 2, kBlock>(max_rows);
+}
+
+static cudaError_t set_max_dyn(const void* f, size_t max_smem) {
+  cudaFuncAttributes a;
+  cudaError_t r = cudaFuncGetAttributes(&a, f);
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(max_smem - a.sharedSizeBytes));
+  return r;
+}
+
+template <int E>
+static const void* tile_kernel(int which) {
+  switch (which) {
+    case 0: return (const void*)k_primal<float, kBlock, E>;
+    case 1: return (const void*)k_primal<double, kBlock, E>;
+    case 2: return (const void*)k_dual<float, kBlock, E>;
+    case 3: return (const void*)k_dual<double, kBlock, E>;
+    case 4: return (const void*)k_eval<float, kBlock, E>;
+    case 5: return (const void*)k_eval<double, kBlock, E>;
+    case 6: return (const void*)k_spmv<float, kBlock, E>;
+    case 7: return (const void*)k_spmv<double, kBlock, E>;
+    default: return nullptr;
+  }
+}
+static const void* fixed_kernel(int which) {
+  switch (which) {
+    case 0: return (const void*)k_report_n<kBlock>;
+    case 1: return (const void*)k_report_m<kBlock>;
+    case 2: return (const void*)k_ws_z<kBlock>;
+    default: return nullptr;
+  }
+}
 
 // raise the dynamic shared-memory limit of every tile kernel
 cudaError_t configure_tile_kernels(size_t max_smem) {
   cudaError_t e = cudaSuccess;
-  auto set = [&](const void* f) {
-    cudaFuncAttributes a;
-    cudaError_t r = cudaFuncGetAttributes(&a, f);
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(max_smem - a.sharedSizeBytes));
+  for (int w = 0; w < 8; ++w)
+    for (const void* f : {tile_kernel<4>(w), tile_kernel<8>(w), tile_kernel<16>(w)}) {
+      cudaError_t r = set_max_dyn(f, max_smem);
+      if (r != cudaSuccess) e = r;
+    }
+  for (int w = 0; w < 3; ++w) {
+    cudaError_t r = set_max_dyn(fixed_kernel(w), max_smem);
     if (r != cudaSuccess) e = r;
-  };
-  set((const void*)k_primal<float, kBlock>);
-  set((const void*)k_primal<double, kBlock>);
-  set((const void*)k_dual<float, kBlock>);
-  set((const void*)k_dual<double, kBlock>);
-  set((const void*)k_eval<float, kBlock>);
-  set((const void*)k_eval<double, kBlock>);
-  set((const void*)k_spmv<float, kBlock>);
-  set((const void*)k_spmv<double, kBlock>);
-  set((const void*)k_report_n<kBlock>);
-  set((const void*)k_report_m<kBlock>);
-  set((const void*)k_ws_z<kBlock>);
+  }
   return e;
 }
 
-// occupancy of the tile kernels (blocks per SM) for a dynamic smem size
-int tile_occupancy(int which, size_t smem) {
-  int nb = 0;
+// blocks per SM of a tile kernel (which: 0/1 primal f32/f64, 2/3 dual,
+// 4/5 eval, 6/7 spmv; 8: the float64 report kernels) at a dynamic smem size
+int tile_occupancy(int which, int e, size_t smem) {
   const void* f = nullptr;
-  switch (which) {
-    case 0: f = (const void*)k_primal<float, kBlock>; break;
-    case 1: f = (const void*)k_primal<double, kBlock>; break;
-    case 2: f = (const void*)k_dual<float, kBlock>; break;
-    case 3: f = (const void*)k_dual<double, kBlock>; break;
-    case 4: f = (const void*)k_eval<float, kBlock>; break;
-    case 5: f = (const void*)k_eval<double, kBlock>; break;
-    default: f = (const void*)k_report_n<kBlock>; break;
-  }
+  if (which >= 8)
+    f = fixed_kernel(0);
+  else if (e == 4)
+    f = tile_kernel<4>(which);
+  else if (e == 16)
+    f = tile_kernel<16>(which);
+  else
+    f = tile_kernel<8>(which);
+  int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kBlock, smem);
   return nb < 1 ? 1 : nb;
 }

@@ -8,6 +8,8 @@
 namespace pdhg {
 
 constexpr int kBlock = 256;       // threads per block of every tile kernel
+constexpr int kFixedE = 8;        // nonzeros per thread of the float64 report,
+                                  // Algorithm 1 and power-iteration schedules
 constexpr int kEvalQ = 2 * Q_N;   // reduced quantities per evaluation
 
 // Device pointers of one LP's iteration state in precision T.
@@ -126,10 +128,7 @@ void launch_init_scalars(Scalars* sc, const double* sums, const PowerState* ps,
                          double eta_safety, cudaStream_t s);
 cudaError_t configure_setup_kernels(size_t max_smem);
 cudaError_t configure_tile_kernels(size_t max_smem);
-int tile_occupancy(int which, size_t smem);
-size_t tile_smem_1f(int tn, int mr);
-size_t tile_smem_1d(int tn, int mr);
-size_t tile_smem_2f(int tn, int mr);
-size_t tile_smem_2d(int tn, int mr);
+int tile_occupancy(int which, int e, size_t smem);
+size_t tile_smem(int nv, bool f32, int max_rows);
 
 }  // namespace pdhg

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(BLOCK) k_pow_Av(SchedView S, const int32_t* rp
     __device__ void row(int r, const double (&s)[1], int) { u[r] = s[0]; }
   } epi{u};
   Gather<double, 1> g{{v}};
-  run_tiles<double, 1, BLOCK>(S, rp, col, val, g, epi, smem);
+  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
 }
 
 struct PowEpi {
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(BLOCK) k_pow_ATu(SchedView S, const int32_t* r
   double* split_q = partials + 2 * (size_t)gridDim.x;
   PowEpi epi{v, w, 0.0, 0.0, split_q};
   Gather<double, 1> g{{u}};
-  run_tiles<double, 1, BLOCK>(S, rp, col, val, g, epi, smem);
+  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
   const double vv[2] = {epi.lam, epi.nw2};
   double o[2];
   block_sum<BLOCK, 2>(vv, o, red);

@@ -12,6 +12,7 @@
 
 #include "kernels.h"
 #include "pdhg.h"
+#include "spmv_tile.cuh"
 
 namespace pdhg {
 void set_error(const char* fmt, ...);
@@ -59,45 +60,29 @@ struct HostSched {
   std::vector<Tile> tiles;
   std::vector<SplitGroup> groups;
   int total_parts = 0;
-  int tile_nnz = 0, max_rows = 0;
+  int tile_nnz = 0, max_rows = 0, e = 8;
 };
 
-static int pow2_floor(int v) {
-  int p = 1;
-  while (p * 2 <= v) p *= 2;
-  return p;
-}
-static int pow2_ceil(int v) {
-  int p = 1;
-  while (p < v) p *= 2;
-  return p;
-}
-
-// threads per row: spread the block over the tile's rows, but no wider than
-// the mean row length needs
-static int lanes_for(int nrows, int64_t nnz) {
-  if (nrows <= 0) return 1;
-  const int by_rows = pow2_floor(std::max(1, kBlock / nrows));
-  const int mean = (int)std::max<int64_t>(1, (nnz + nrows - 1) / nrows);
-  const int by_len = pow2_ceil(mean);
-  return std::max(1, std::min(by_rows, std::min(by_len, kBlock)));
-}
-
-static HostSched build_sched(const int32_t* rp, int nrows, int tile_nnz) {
+// Tiles: runs of whole rows with at most tile_capacity(kBlock, e) nonzeros
+// and at most tile_max_rows(kBlock) rows; a longer row becomes a split group
+// of capacity-sized chunks.
+static HostSched build_sched(const int32_t* rp, int nrows, int e) {
   HostSched h;
-  h.tile_nnz = tile_nnz;
-  h.max_rows = tile_nnz;
+  const int cap = tile_capacity(kBlock, e);
+  h.tile_nnz = cap;
+  h.max_rows = tile_max_rows(kBlock);
+  h.e = e;
   int r = 0;
   while (r < nrows) {
     const int64_t len = (int64_t)rp[r + 1] - rp[r];
-    if (len > tile_nnz) {
-      const int nparts = (int)((len + tile_nnz - 1) / tile_nnz);
+    if (len > cap) {
+      const int nparts = (int)((len + cap - 1) / cap);
       const int gid = (int)h.groups.size();
       h.groups.push_back(SplitGroup{r, nparts, h.total_parts, 0});
       for (int p = 0; p < nparts; ++p) {
-        const int64_t b = rp[r] + (int64_t)p * tile_nnz;
-        const int64_t e = std::min<int64_t>(b + tile_nnz, rp[r + 1]);
-        h.tiles.push_back(Tile{r, r + 1, (int32_t)b, (int32_t)e, gid, p, kBlock, 0});
+        const int64_t b = rp[r] + (int64_t)p * cap;
+        const int64_t en = std::min<int64_t>(b + cap, rp[r + 1]);
+        h.tiles.push_back(Tile{r, r + 1, (int32_t)b, (int32_t)en, gid, p, 0, 0});
       }
       h.total_parts += nparts;
       ++r;
@@ -107,12 +92,11 @@ static HostSched build_sched(const int32_t* rp, int nrows, int tile_nnz) {
     int64_t nz = 0;
     while (r < nrows && r - start < h.max_rows) {
       const int64_t l = (int64_t)rp[r + 1] - rp[r];
-      if (l > tile_nnz || nz + l > tile_nnz) break;
+      if (l > cap || nz + l > cap) break;
       nz += l;
       ++r;
     }
-    const int nr = r - start;
-    h.tiles.push_back(Tile{start, r, rp[start], rp[r], -1, 0, lanes_for(nr, nz), 0});
+    h.tiles.push_back(Tile{start, r, rp[start], rp[r], -1, 0, 0, 0});
   }
   return h;
 }
@@ -166,7 +150,8 @@ struct pdhg_ctx {
   double* log_kkt = nullptr;
   int log_cap = 4096;
   // schedules and launch shapes
-  DevSched sa, st;
+  DevSched sa, st;      // iteration schedules (autotuned nonzeros per thread)
+  DevSched sa8, st8;    // float64 report / Algorithm 1 / power iteration
   Launch l_prim{}, l_dual{}, l_eval{}, l_a64{}, l_t64{};
   int restart_grid = 1;
   // graphs and polling
@@ -214,12 +199,11 @@ static pdhg_status copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t by
   return PDHG_OK;
 }
 
-static size_t smem_for(int kind, bool mixed, int tile_nnz, int max_rows) {
-  // kind 0: NV = 1 in iteration precision, 1: NV = 2 in iteration precision,
-  // 2: NV = 1 float64
-  if (kind == 0) return mixed ? tile_smem_1f(tile_nnz, max_rows) : tile_smem_1d(tile_nnz, max_rows);
-  if (kind == 1) return mixed ? tile_smem_2f(tile_nnz, max_rows) : tile_smem_2d(tile_nnz, max_rows);
-  return tile_smem_1d(tile_nnz, max_rows);
+// kind 0: one gathered vector in the iteration precision, 1: two, 2: one in float64
+static size_t smem_for(int kind, bool mixed, int max_rows) {
+  if (kind == 0) return tile_smem(1, mixed, max_rows);
+  if (kind == 1) return tile_smem(2, mixed, max_rows);
+  return tile_smem(1, false, max_rows);
 }
 
 static pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) {
@@ -244,21 +228,22 @@ static pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) 
   d->view.tile_nnz = h.tile_nnz;
   d->view.max_rows = h.max_rows;
   d->view.ngroups = (int32_t)h.groups.size();
+  d->view.e = h.e;
   // make the host vectors' lifetime irrelevant: copies are enqueued, wait here
   CK(cudaStreamSynchronize(ctx->stream));
   return PDHG_OK;
 }
 
-static Launch make_launch(pdhg_ctx* ctx, int occ_kind, size_t smem, int ntiles) {
-  const int occ = tile_occupancy(occ_kind, smem);
+static Launch make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int ntiles) {
+  const int occ = tile_occupancy(occ_kind, e, smem);
   int grid = std::min(ntiles, ctx->nsm * occ);
   return Launch{std::max(grid, 1), smem};
 }
 
 // Time one SpMV schedule candidate (mean of a few launches after warm-up).
 static pdhg_status time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float* ms_out) {
-  const size_t smem = smem_for(0, ctx->mixed, d.view.tile_nnz, d.view.max_rows);
-  Launch L = make_launch(ctx, ctx->mixed ? 0 : 1, smem, d.view.ntiles);
+  const size_t smem = smem_for(0, ctx->mixed, d.view.max_rows);
+  Launch L = make_launch(ctx, ctx->mixed ? 6 : 7, d.view.e, smem, d.view.ntiles);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -296,19 +281,19 @@ static pdhg_status time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float*
 static pdhg_status choose_schedules(pdhg_ctx* ctx) {
   std::vector<int> cands;
   if (ctx->opt.tile_nnz > 0)
-    cands.push_back(ctx->opt.tile_nnz);
+    cands.push_back(ctx->opt.tile_nnz <= 1024 ? 4 : (ctx->opt.tile_nnz <= 2048 ? 8 : 16));
   else if (ctx->opt.autotune)
-    cands = {512, 1024, 2048, 4096};
+    cands = {4, 8, 16};
   else
-    cands = {2048};
+    cands = {8};
   for (int which = 0; which < 2; ++which) {
     const bool on_a = which == 0;
     const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
     const int nrows = on_a ? ctx->m : ctx->n;
     DevSched best{};
     float best_ms = 1e30f;
-    for (int tn : cands) {
-      HostSched h = build_sched(rp.data(), nrows, tn);
+    for (int e : cands) {
+      HostSched h = build_sched(rp.data(), nrows, e);
       DevSched d;
       CKS(upload_sched(ctx, h, &d));
       float ms = 0.f;
@@ -319,26 +304,34 @@ static pdhg_status choose_schedules(pdhg_ctx* ctx) {
       }
     }
     (on_a ? ctx->sa : ctx->st) = best;
+    // the float64 kernels (report, Algorithm 1, power iteration) use kFixedE
+    if (best.view.e == kFixedE) {
+      (on_a ? ctx->sa8 : ctx->st8) = best;
+    } else {
+      HostSched h = build_sched(rp.data(), nrows, kFixedE);
+      CKS(upload_sched(ctx, h, on_a ? &ctx->sa8 : &ctx->st8));
+    }
   }
   // launch shapes
   const bool mx = ctx->mixed;
   const SchedView &A = ctx->sa.view, &T = ctx->st.view;
-  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, smem_for(0, mx, T.tile_nnz, T.max_rows), T.ntiles);
-  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, smem_for(0, mx, A.tile_nnz, A.max_rows), A.ntiles);
+  const SchedView &A8 = ctx->sa8.view, &T8 = ctx->st8.view;
+  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, T.e, smem_for(0, mx, T.max_rows), T.ntiles);
+  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, A.e, smem_for(0, mx, A.max_rows), A.ntiles);
   {
-    const size_t sm = smem_for(1, mx, T.tile_nnz, T.max_rows);
-    const int occ = tile_occupancy(mx ? 4 : 5, sm);
+    const size_t sm = smem_for(1, mx, T.max_rows);
+    const int occ = tile_occupancy(mx ? 4 : 5, T.e, sm);
     // the eval kernel also walks the m rows elementwise: at least enough blocks for that
     int grid = std::max(T.ntiles, (ctx->m + kBlock - 1) / kBlock);
     grid = std::max(1, std::min(grid, ctx->nsm * occ));
     ctx->l_eval = Launch{grid, sm};
   }
-  ctx->l_a64 = make_launch(ctx, 6, smem_for(2, mx, A.tile_nnz, A.max_rows), A.ntiles);
-  ctx->l_t64 = make_launch(ctx, 6, smem_for(2, mx, T.tile_nnz, T.max_rows), T.ntiles);
+  ctx->l_a64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, A8.max_rows), A8.ntiles);
+  ctx->l_t64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, T8.max_rows), T8.ntiles);
   ctx->restart_grid = std::max(1, std::min(ctx->nsm * 8, (std::max(ctx->m, ctx->n) + 255) / 256));
   // reduction scratch: the largest grid plus split records, kEvalQ doubles each
   const int gmax = std::max({ctx->l_eval.grid, ctx->l_a64.grid, ctx->l_t64.grid, 4096});
-  const int groups = std::max(A.ngroups, T.ngroups);
+  const int groups = std::max({A.ngroups, T.ngroups, A8.ngroups, T8.ngroups});
   ctx->partials_len = (size_t)(gmax + groups + 1) * kEvalQ;
   CKS(dalloc(ctx, &ctx->partials, ctx->partials_len));
   CKS(dalloc(ctx, &ctx->split_q, (size_t)(T.ngroups + 1) * kEvalQ));
@@ -649,9 +642,9 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     launch_pow_init(n, v, ctx->ps, ctx->opt.power_max_iter, ctx->opt.power_rel_tol, ctx->stream);
     ctx->launches += 1;
     for (int it = 0; it < ctx->opt.power_max_iter; ++it) {
-      launch_pow_Av(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64, v, u, ctx->ps, ctx->l_a64,
+      launch_pow_Av(ctx->sa8.view, ctx->a_rp, ctx->a_col, ctx->a_val64, v, u, ctx->ps, ctx->l_a64,
                     ctx->stream);
-      launch_pow_ATu(ctx->st.view, ctx->t_rp, ctx->t_col, ctx->t_val64, u, v, w, ctx->partials,
+      launch_pow_ATu(ctx->st8.view, ctx->t_rp, ctx->t_col, ctx->t_val64, u, v, w, ctx->partials,
                      ctx->ps, ctx->l_t64, ctx->stream);
       launch_pow_norm(n, w, v, ctx->ps, ctx->stream);
       ctx->launches += 3;
@@ -885,12 +878,12 @@ static pdhg_status compute_report(pdhg_ctx* ctx) {
   const double *xs, *ys;
   CKS(returned_iterate64(ctx, &xs, &ys));
   double* pn = ctx->partials;
-  const int gn = ctx->l_t64.grid + ctx->st.view.ngroups;
+  const int gn = ctx->l_t64.grid + ctx->st8.view.ngroups;
   double* pm = ctx->partials + 4 * (size_t)(gn + 1);
-  const int gm = ctx->l_a64.grid + ctx->sa.view.ngroups;
-  launch_report_n(ctx->st.view, ctx->t_rp, ctx->t_col, ctx->t_val64, xs, ys, ctx->c_t64, ctx->D_c,
+  const int gm = ctx->l_a64.grid + ctx->sa8.view.ngroups;
+  launch_report_n(ctx->st8.view, ctx->t_rp, ctx->t_col, ctx->t_val64, xs, ys, ctx->c_t64, ctx->D_c,
                   ctx->out_n1, ctx->out_n2, pn, ctx->l_t64, ctx->stream);
-  launch_report_m(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64, xs, ys, ctx->b_t64, ctx->D_r,
+  launch_report_m(ctx->sa8.view, ctx->a_rp, ctx->a_col, ctx->a_val64, xs, ys, ctx->b_t64, ctx->D_r,
                   ctx->out_m1, pm, ctx->l_a64, ctx->stream);
   launch_report_final(pn, gn, pm, gm, ctx->report, ctx->stream);
   ctx->launches += 3;
@@ -958,9 +951,9 @@ extern "C" pdhg_status pdhg_warmstart_point(pdhg_ctx* ctx, double mu_min, double
   CKS(returned_iterate64(ctx, &xs, &ys));
   double* zs = ctx->out_n2;
   double* mu = ctx->report + 7;
-  launch_ws_z(ctx->st.view, ctx->t_rp, ctx->t_col, ctx->t_val64, xs, ys, ctx->c_t64, zs,
+  launch_ws_z(ctx->st8.view, ctx->t_rp, ctx->t_col, ctx->t_val64, xs, ys, ctx->c_t64, zs,
               ctx->partials, ctx->l_t64, ctx->stream);
-  launch_ws_mu(ctx->partials, ctx->l_t64.grid + ctx->st.view.ngroups, ctx->n, mu_min, mu,
+  launch_ws_mu(ctx->partials, ctx->l_t64.grid + ctx->st8.view.ngroups, ctx->n, mu_min, mu,
                ctx->stream);
   // outputs land in out_n1 (x'), out_m1 (y), and z' overwrites z~ in place
   launch_ws_apply(ctx->n, ctx->m, xs, zs, ys, mu, delta_max, alpha_min, unscaled, ctx->D_r,
@@ -1089,7 +1082,6 @@ extern "C" pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const doub
   CKS(state_in(ctx, ctx->y_avg, y_avg, m));
   CKS(state_in(ctx, ctx->y_last, y_last, m));
   // caches A~x and A~x_avg in the iteration precision
-  const size_t smem = smem_for(0, ctx->mixed, ctx->sa.view.tile_nnz, ctx->sa.view.max_rows);
   if (ctx->mixed) {
     launch_spmv<float>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val32, (const float*)ctx->x,
                        (float*)ctx->Ax, ctx->l_dual, ctx->stream);
@@ -1101,7 +1093,6 @@ extern "C" pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const doub
     launch_spmv<double>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64,
                         (const double*)ctx->x_avg, (double*)ctx->Ax_avg, ctx->l_dual, ctx->stream);
   }
-  (void)smem;
   Scalars hs;
   CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

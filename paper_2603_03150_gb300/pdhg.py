@@ -136,10 +136,6 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-def _out_ptr(x, dtype=ctypes.c_double):
-    return ctypes.byref(x)
-
-
 class Solver:
     """One LP  min c^T x, Ax = b, x >= 0  held by a library context.
 
@@ -172,11 +168,11 @@ class Solver:
         self.device_io = device_io
         self.mixed = o.precision == FP32_MIXED
         if not device_io:
-            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
-            col = np.ascontiguousarray(col, dtype=np.int32)
-            val = np.ascontiguousarray(val, dtype=np.float64)
-            b = np.ascontiguousarray(b, dtype=np.float64)
-            c = np.ascontiguousarray(c, dtype=np.float64)
+            # host tensors (e.g. pinned torch CPU tensors) pass through as they are
+            def host(a, dt):
+                return a if _is_torch(a) else np.ascontiguousarray(a, dtype=dt)
+            row_ptr, col = host(row_ptr, np.int32), host(col, np.int32)
+            val, b, c = host(val, np.float64), host(b, np.float64), host(c, np.float64)
         self._ctx = ctypes.c_void_p()
         self._L = L
         st = L.pdhg_create(ctypes.byref(self._ctx), self.m, self.n, _ptr(row_ptr), _ptr(col),
@@ -199,23 +195,29 @@ class Solver:
         self.status = _check(self._L.pdhg_solve(self._ctx, eps_rel, max_iter))
         return self.status
 
-    def get(self):
-        x, y, z = self._new(self.n), self._new(self.m), self._new(self.n)
+    def get(self, out=None):
+        """Returned iterate (x, y, z) and its residual norms; ``out`` may hold
+        preallocated (x, y, z) buffers."""
+        x, y, z = out if out is not None else (self._new(self.n), self._new(self.m), self._new(self.n))
         rp, rd, gap = _D(), _D(), _D()
         _check(self._L.pdhg_get(self._ctx, _ptr(x), _ptr(y), _ptr(z), ctypes.byref(rp),
                                 ctypes.byref(rd), ctypes.byref(gap)))
         return dict(x=x, y=y, z=z, r_P=rp.value, r_D=rd.value, gap=gap.value)
 
-    def info(self):
+    def info(self, violation: bool = True):
+        """Counters; ``violation=False`` skips the float64 report (no GPU work)."""
         it, rs, mv, ca, ls = _I64(), _I64(), _D(), _I32(), _I32()
         _check(self._L.pdhg_get_info(self._ctx, ctypes.byref(it), ctypes.byref(rs),
-                                     ctypes.byref(mv), ctypes.byref(ca), ctypes.byref(ls)))
-        return dict(iters=it.value, restarts=rs.value, max_violation=mv.value,
+                                     ctypes.byref(mv) if violation else None,
+                                     ctypes.byref(ca), ctypes.byref(ls)))
+        return dict(iters=it.value, restarts=rs.value,
+                    max_violation=mv.value if violation else None,
                     chosen_average=bool(ca.value), status=ls.value)
 
     def warmstart_point(self, mu_min: float = 1e-6, delta_max: float = 1e-4,
-                        alpha_min: float = 1e-6, unscaled: bool = False):
-        x, y, z = self._new(self.n), self._new(self.m), self._new(self.n)
+                        alpha_min: float = 1e-6, unscaled: bool = False, out=None):
+        """Algorithm 1 start point (x', y, z') and mu_target."""
+        x, y, z = out if out is not None else (self._new(self.n), self._new(self.m), self._new(self.n))
         mu = _D()
         _check(self._L.pdhg_warmstart_point(self._ctx, mu_min, delta_max, alpha_min,
                                             1 if unscaled else 0, _ptr(x), _ptr(y), _ptr(z),
