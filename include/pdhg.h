@@ -167,6 +167,32 @@ pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int32_t* a_blo
                               int32_t* a_tiles, int32_t* at_tile_nnz, int32_t* at_block,
                               int32_t* at_tiles);
 
+/* Algorithm 1's centered start point (as pdhg_warmstart_point, scaled
+ * output) for caller-provided DEVICE vectors, allocating no device memory.
+ * The paper has no counterpart of this entry point: it exists for callers
+ * that cannot call cudaMalloc -- code that runs while its stream is being
+ * captured into a CUDA graph (allocation is not capturable), an
+ * interior-point solver that owns a fixed device memory pool, or a thread
+ * that must not take the allocator's locks.
+ *  n              entries, 1 <= n <= 8,388,608 (larger n -> PDHG_INVALID_ARG;
+ *                 the static scratch holds 4096 partial sums of 2048 entries)
+ *  x, z           device float64[n]: the PDHG x and z of the scaled LP
+ *  x_out, z_out   device float64[n]: x' and z' (may not alias x or z)
+ *  mu_target      device float64[1] receiving mu, or NULL
+ *  stream         cudaStream_t to run on (NULL: the legacy default stream)
+ * The scratch is one file-scope device array per GPU that loads the library
+ * (32 KB, held until the process exits), shared by every call: calls whose
+ * work overlaps on the GPU race and must be serialised by the caller (for
+ * example by using one stream).  Each call writes every scratch slot it
+ * reads, so nothing needs clearing between calls.  The first call on a
+ * device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  The call is
+ * asynchronous: results are ready when `stream` reaches it.  */
+pdhg_status pdhg_centered_point_noalloc(int32_t n, const double* x, const double* z,
+                                        double mu_min, double delta_max, double alpha_min,
+                                        double* x_out, double* z_out, double* mu_target,
+                                        void* stream);
+
 /* Kernels this context has launched since pdhg_create (graph replays count
  * every kernel node).  */
 pdhg_status pdhg_get_launch_count(pdhg_ctx* ctx, int64_t* launches);

@@ -83,6 +83,7 @@ _SIGS = {
     "pdhg_get_kernel_timing": (_I32, [_P, _P, _P, _P]),
     "pdhg_get_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "pdhg_get_launch_count": (_I32, [_P, _P]),
+    "pdhg_centered_point_noalloc": (_I32, [_I32, _P, _P, _D, _D, _D, _P, _P, _P, _P]),
     "pdhg_destroy": (None, [_P]),
     "pdhg_last_error": (ctypes.c_char_p, []),
 }
@@ -134,6 +135,16 @@ def _ptr(a):
         return ctypes.c_void_p(a.data_ptr())
     assert a.flags["C_CONTIGUOUS"]
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def centered_point_noalloc(x, z, x_out, z_out, mu_target=None, mu_min: float = 1e-6,
+                           delta_max: float = 1e-4, alpha_min: float = 1e-6, stream=None) -> None:
+    """Algorithm 1 start point of device vectors (CUDA float64 tensors) into
+    caller-provided outputs, with no device allocation by the library."""
+    n = int(x.numel())
+    _check(lib().pdhg_centered_point_noalloc(n, _ptr(x), _ptr(z), mu_min, delta_max, alpha_min,
+                                             _ptr(x_out), _ptr(z_out), _ptr(mu_target), stream),
+           allow_positive=False)
 
 
 class Solver:
