@@ -124,20 +124,20 @@ def peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ["spmv_tile.cuh", "iter_kernels.cu", "common.cuh", "kernels.h"]:
+    for f in ["spmv_tile.cuh", "iter_kernels.cu", "common.cuh"]:
         h.update(open(os.path.join(ROOT, "paper_2603_03150_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, precision: str, workload: str):
+def ncu_traffic(kernel: str, precision: str, workload: str, e_per_thread: int):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    the current kernel sources and the same schedule variant (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
-    e = d.get(f"{workload}/{precision}/{kernel}")
+    e = d.get(f"{workload}/{precision}/{kernel}/E{e_per_thread}")
     if not e or e.get("source_sha") != kernel_source_sha():
         return None
     return e.get("bytes_per_launch")
@@ -263,7 +263,10 @@ def run_ours(args):
     peak, peak_src = peaks()
     ach = ab[dom] / (dur / 1e3) / 1e9 if dur > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": ncu_traffic(dom, args.precision, args.workload),
+                "frac": round(ach / peak, 4),
+                "traffic": ncu_traffic("k_primal" if dom == "primal" else "k_dual", args.precision,
+                                       args.workload,
+                                       (rec[0]["sched"]["at_tile_nnz" if dom == "primal" else "a_tile_nnz"] + 4) // 256),
                 "kernel": "k_primal" if dom == "primal" else "k_dual",
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": ab[dom],
                 "mean_launch_ms": round(dur, 5), "samples": ns,

@@ -247,7 +247,7 @@ static pdhg_status time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float*
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int warm = 2, reps = 5;
+  const int warm = 3, reps = 10;
   ctx->launches += warm + reps;
   for (int it = 0; it < warm + reps; ++it) {
     if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
@@ -298,8 +298,11 @@ static pdhg_status choose_schedules(pdhg_ctx* ctx) {
       CKS(upload_sched(ctx, h, &d));
       float ms = 0.f;
       if (cands.size() > 1) CKS(time_spmv(ctx, d, on_a, &ms));
-      if (ms < best_ms) {
-        best_ms = ms;
+      // E = 8 is kept unless another choice is more than 3% faster, so timing
+      // noise does not flip the schedule from one context to the next
+      const float bias = (e == 8) ? 0.97f : 1.0f;
+      if (ms * bias < best_ms) {
+        best_ms = ms * bias;
         best = d;
       }
     }
