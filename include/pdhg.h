@@ -167,6 +167,45 @@ pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int32_t* a_blo
                               int32_t* a_tiles, int32_t* at_tile_nnz, int32_t* at_block,
                               int32_t* at_tiles);
 
+/* ---- batched solves -------------------------------------------------------
+ * `count` independent LPs iterated together as one block-diagonal system: each
+ * LP keeps its own scaling, step sizes, primal weight, restart state and
+ * status (Section 2 test per LP); an LP that has passed its test is masked
+ * while the others continue.  Sizes are given per LP; arrays are the
+ * concatenation over LPs in order:
+ *  m, n       HOST int32[count], each >= 1
+ *  row_ptr    int32[sum(m) + count]: each LP's own row pointer (starting at 0)
+ *  col        int32[sum nnz]: each LP's local column indices, strictly
+ *             increasing within a row, in [0, n_l)
+ *  val        float64[sum nnz];  b float64[sum m];  c float64[sum n]
+ * Pointers are host or device as for pdhg_create (options.io_on_device).
+ * Totals of rows, columns and nonzeros must fit in int32.  */
+pdhg_status pdhg_batch_create(pdhg_ctx** out, int32_t count, const int32_t* m, const int32_t* n,
+                              const int32_t* row_ptr, const int32_t* col, const double* val,
+                              const double* b, const double* c, const pdhg_options* opt);
+
+/* Iterate every LP (in lockstep, F iterations per chunk) until each has
+ * passed the Section 2 test with eps_rel or the iteration count reaches
+ * max_iter.  lp_status (HOST int32[count] or NULL) receives each LP's
+ * status; the return value is the largest of them (PDHG_CONVERGED only if
+ * all converged).  */
+pdhg_status pdhg_batch_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_iter,
+                             int32_t* lp_status);
+
+/* Returned iterates in the original models, concatenated: x[sum n], y[sum m],
+ * z[sum n]; per LP (HOST arrays [count], NULL skips): ||r_P||_2, ||r_D||_2,
+ * |c^T x - b^T y|, the Section 4.3 maximum violation, iterations done.  */
+pdhg_status pdhg_batch_get(pdhg_ctx* ctx, double* x, double* y, double* z, double* lp_r_P,
+                           double* lp_r_D, double* lp_gap, double* lp_max_violation,
+                           int64_t* lp_iters);
+
+/* Algorithm 1 (Section 3.1) for every LP of the batch, as
+ * pdhg_warmstart_point; lp_mu (HOST float64[count] or NULL) receives each
+ * LP's mu_target.  */
+pdhg_status pdhg_batch_warmstart_point(pdhg_ctx* ctx, double mu_min, double delta_max,
+                                       double alpha_min, int32_t unscaled, double* x_ws,
+                                       double* y_ws, double* z_ws, double* lp_mu);
+
 /* Algorithm 1's centered start point (as pdhg_warmstart_point, scaled
  * output) for caller-provided DEVICE vectors, allocating no device memory.
  * The paper has no counterpart of this entry point: it exists for callers

@@ -19,7 +19,8 @@ struct Tile {
   int32_t nz_begin, nz_end;    // nonzeros [nz_begin, nz_end)
   int32_t split;               // -1: whole rows; else split-group index
   int32_t part;                // chunk index within the split group
-  int32_t pad0, pad1;
+  int32_t lp;                  // LP of the tile's rows (batched solves; 0 otherwise)
+  int32_t pad;
 };
 
 struct SplitGroup {

@@ -1,0 +1,160 @@
+// Host-side context of a solver (single LP or a batch of LPs) shared by the
+// translation units of the C ABI.
+#pragma once
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "pdhg.h"
+#include "spmv_tile.cuh"
+
+namespace pdhg {
+void set_error(const char* fmt, ...);
+void clear_error();
+}  // namespace pdhg
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      pdhg::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                __LINE__);                                                          \
+      return e_ == cudaErrorMemoryAllocation ? PDHG_OOM : PDHG_CUDA_ERROR;          \
+    }                                                                               \
+  } while (0)
+
+#define CKS(expr)                          \
+  do {                                     \
+    pdhg_status s_ = (expr);               \
+    if (s_ < 0) return s_;                 \
+  } while (0)
+
+
+namespace pdhg {
+
+struct HostSched {
+  std::vector<Tile> tiles;
+  std::vector<SplitGroup> groups;
+  int total_parts = 0;
+  int tile_nnz = 0, max_rows = 0, e = 8;
+  std::vector<int32_t> lp_tiles;  // [count + 1] first tile of each LP
+};
+
+// Tiles of whole rows (at most tile_capacity(kBlock, e) nonzeros and
+// tile_max_rows(kBlock) rows) or capacity-sized chunks of a longer row.
+// With lp_off (count + 1 row offsets) no tile crosses an LP boundary and each
+// tile records its LP.
+HostSched build_sched(const int32_t* rp, int nrows, int e, const int64_t* lp_off = nullptr,
+                      int count = 1);
+
+struct DevSched {
+  Tile* tiles = nullptr;
+  SplitGroup* groups = nullptr;
+  int32_t* counters = nullptr;
+  double* slots = nullptr;
+  SchedView view{};
+};
+
+}  // namespace pdhg
+
+using pdhg::DevSched;
+using pdhg::Launch;
+using pdhg::PowerState;
+using pdhg::Scalars;
+
+struct pdhg_ctx {
+  int m = 0, n = 0;
+  int64_t nnz = 0, nnz_pad = 0;
+  pdhg_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int nsm = 0;
+  size_t smem_optin = 0;
+  bool mixed = false;
+
+  std::vector<void*> allocs;
+  // matrices
+  int32_t *a_rp = nullptr, *a_col = nullptr, *t_rp = nullptr, *t_col = nullptr;
+  double *a_val_orig = nullptr, *t_val_orig = nullptr, *a_val64 = nullptr, *t_val64 = nullptr;
+  float *a_val32 = nullptr, *t_val32 = nullptr;
+  std::vector<int32_t> h_a_rp, h_t_rp;
+  // vectors
+  double *b = nullptr, *c = nullptr, *b_t64 = nullptr, *c_t64 = nullptr, *D_r = nullptr,
+         *D_c = nullptr;
+  float *b_t32 = nullptr, *c_t32 = nullptr;
+  void *x = nullptr, *y = nullptr, *x_avg = nullptr, *y_avg = nullptr, *x_last = nullptr,
+       *y_last = nullptr, *Ax = nullptr, *Ax_avg = nullptr;
+  double *xs64 = nullptr, *ys64 = nullptr, *out_n1 = nullptr, *out_n2 = nullptr,
+         *out_m1 = nullptr, *report = nullptr, *sums = nullptr;
+  Scalars* sc = nullptr;
+  PowerState* ps = nullptr;
+  double* partials = nullptr;  // generic reduction scratch
+  size_t partials_len = 0;
+  double* split_q = nullptr;
+  long long* log_k = nullptr;
+  int32_t* log_flags = nullptr;
+  double* log_kkt = nullptr;
+  int log_cap = 4096;
+  // batched solves: `count` independent LPs as one block-diagonal system
+  int count = 1;
+  bool batch = false;
+  std::vector<int64_t> h_m_off, h_n_off;  // [count + 1] row / column offsets
+  int32_t *lp_a_tiles = nullptr, *lp_t_tiles = nullptr;    // [count + 1] tile ranges
+  int32_t *lp_a8_tiles = nullptr, *lp_t8_tiles = nullptr;  // same, float64 schedules
+  double *rec_t = nullptr, *rec_a = nullptr;  // per-tile evaluation / report records
+  int32_t* active = nullptr;                  // LPs not finished after the last evaluation
+  double* breport = nullptr;                  // [count][8] per-LP report
+  // schedules and launch shapes
+  DevSched sa, st;      // iteration schedules (autotuned nonzeros per thread)
+  DevSched sa8, st8;    // float64 report / Algorithm 1 / power iteration
+  Launch l_prim{}, l_dual{}, l_eval{}, l_a64{}, l_t64{};
+  int restart_grid = 1;
+  // graphs and polling
+  cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  cudaEvent_t ev_k[2][4] = {};
+  Scalars* h_sc[2] = {nullptr, nullptr};
+  double timing_sum[2] = {0, 0};
+  long long timing_n = 0;
+  // cached host data
+  double omega0 = 1.0;
+  int power_iters = 0;
+  double report_h[8] = {0};
+  long long launches = 0;  // kernels launched (graph replays count every node)
+  bool report_valid = false;
+  int last_status = PDHG_MAX_ITER;
+};
+
+namespace pdhg {
+
+template <typename T>
+pdhg_status dalloc(pdhg_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    pdhg::set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PDHG_OOM : PDHG_CUDA_ERROR;
+  }
+  ctx->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return PDHG_OK;
+}
+
+pdhg_status copy_in(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes);
+pdhg_status copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes);
+// kind 0: one gathered vector in the iteration precision, 1: two, 2: one in float64
+size_t smem_for(int kind, bool mixed, int max_rows);
+pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d);
+Launch make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int ntiles);
+size_t elem(const pdhg_ctx* ctx);
+// create stages shared by the single-LP and batched paths
+pdhg_status setup_device(pdhg_ctx* ctx);
+pdhg_status alloc_arrays(pdhg_ctx* ctx);
+pdhg_status upload_lp(pdhg_ctx* ctx, const int32_t* col, const double* val, const double* b,
+                      const double* c);
+pdhg_status prepare_matrix(pdhg_ctx* ctx);
+pdhg_status polling_resources(pdhg_ctx* ctx);
+
+}  // namespace pdhg

@@ -4,6 +4,7 @@
 // an iterate, and Algorithm 1 (centered start point, Section 3.1).
 #include <math.h>
 
+#include "eval_rule.cuh"
 #include "kernels.h"
 #include "spmv_tile.cuh"
 
@@ -125,85 +126,6 @@ struct EvalEpi {
   }
 };
 
-__device__ __forceinline__ bool finite3(double a, double b, double c) {
-  return isfinite(a) && isfinite(b) && isfinite(c);
-}
-
-// Termination test (Section 2) and the restart rule; runs in one thread.
-template <typename T>
-__device__ void eval_finalize(const IterBuffers<T>& B, const double* tot, int chunk) {
-  Scalars& sc = *B.sc;
-  sc.k += chunk;
-  sc.t += chunk;
-  for (int c = 0; c < 2; ++c)
-    for (int k = 0; k < Q_N; ++k) sc.q[c][k] = tot[c * Q_N + k];
-  bool term[2];
-  bool bad = false;
-  for (int c = 0; c < 2; ++c) {
-    const double* q = tot + c * Q_N;
-    const double rp = sqrt(q[Q_U1]), rd = sqrt(q[Q_U2]);
-    const double pobj = q[Q_S3], dobj = q[Q_S4];
-    if (!finite3(rp, rd, pobj - dobj)) bad = true;
-    term[c] = rp <= sc.eps * (1.0 + sc.norm_b) && rd <= sc.eps * (1.0 + sc.norm_c) &&
-              fabs(pobj - dobj) <= sc.eps * (1.0 + fabs(pobj) + fabs(dobj));
-  }
-  sc.restart_pending = 0;
-  if (term[0] || term[1]) {
-    sc.done = 1;
-    sc.status = 0;
-    sc.chosen_avg = term[0] ? 0 : 1;
-    return;
-  }
-  if (bad) {
-    sc.done = 1;
-    sc.status = 2;
-    sc.chosen_avg = 0;
-    return;
-  }
-  if (sc.k >= sc.max_iter) {
-    sc.done = 1;
-    sc.status = 1;
-    sc.chosen_avg = 0;
-    return;
-  }
-  if (sc.k % sc.eval_freq != 0) return;
-  const double w2 = sc.omega * sc.omega;
-  double kkt[2];
-  for (int c = 0; c < 2; ++c) {
-    const double* q = tot + c * Q_N;
-    const double gap = q[Q_S3] - q[Q_S4];
-    kkt[c] = sqrt(w2 * q[Q_S1] + q[Q_S2] / w2 + gap * gap);
-  }
-  const int cand = (kkt[1] < kkt[0]) ? 1 : 0;
-  const double kc = kkt[cand];
-  const bool r1 = kc <= sc.beta_suff * sc.kkt_last;
-  const bool r2 = (kc <= sc.beta_nec * sc.kkt_last) && (kc > sc.kkt_prev);
-  const bool r3 = (double)sc.t >= sc.beta_art * (double)sc.k;
-  const bool restart = r1 || r2 || r3;
-  if (sc.log_count < sc.log_cap) {
-    const int e = sc.log_count++;
-    B.log_k[e] = sc.k;
-    B.log_flags[e] = (restart ? 1 : 0) | (cand << 1) | (r1 << 2) | (r2 << 3) | (r3 << 4);
-    B.log_kkt[3 * e + 0] = kkt[0];
-    B.log_kkt[3 * e + 1] = kkt[1];
-    B.log_kkt[3 * e + 2] = sc.omega;
-  }
-  sc.kkt_prev = kc;
-  if (restart) {
-    const double dx = sqrt(tot[cand * Q_N + Q_D1]);
-    const double dy = sqrt(tot[cand * Q_N + Q_D2]);
-    if (dx > 1e-10 && dy > 1e-10)
-      sc.omega = exp(sc.theta * log(dy / dx) + (1.0 - sc.theta) * log(sc.omega));
-    sc.tau = sc.eta / sc.omega;
-    sc.sigma = sc.eta * sc.omega;
-    sc.t = 0;
-    sc.restarts += 1;
-    sc.kkt_last = kc;
-    sc.restart_pending = 1;
-    sc.restart_to_avg = cand;
-  }
-}
-
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
   if (B.sc->done) return;
@@ -258,7 +180,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
   __syncthreads();
   if (threadIdx.x == 0) {
     B.sc->ticket = 0;
-    eval_finalize(B, tot, chunk);
+    apply_eval_rule(*B.sc, tot, chunk, B.log_k, B.log_flags, B.log_kkt);
   }
 }
 

@@ -10,13 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "kernels.h"
-#include "pdhg.h"
-#include "spmv_tile.cuh"
-
-namespace pdhg {
-void set_error(const char* fmt, ...);
-}
+#include "context.h"
 
 // ---------------------------------------------------------------------------
 // error reporting
@@ -32,48 +26,46 @@ void pdhg::set_error(const char* fmt, ...) {
   g_last_error = buf;
 }
 using pdhg::set_error;
-
-extern "C" const char* pdhg_last_error(void) { return g_last_error.c_str(); }
-
+#undef CK
 #define CK(call)                                                                    \
   do {                                                                              \
     cudaError_t e_ = (call);                                                        \
     if (e_ != cudaSuccess) {                                                        \
-      set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
-                __LINE__);                                                          \
+      pdhg::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                      __LINE__);                                                    \
       return e_ == cudaErrorMemoryAllocation ? PDHG_OOM : PDHG_CUDA_ERROR;          \
     }                                                                               \
   } while (0)
 
-#define CKS(expr)                          \
-  do {                                     \
-    pdhg_status s_ = (expr);               \
-    if (s_ < 0) return s_;                 \
-  } while (0)
+void pdhg::clear_error() { g_last_error.clear(); }
+
+extern "C" const char* pdhg_last_error(void) { return g_last_error.c_str(); }
 
 namespace pdhg {
 
 // ---------------------------------------------------------------------------
 // tile schedule (host build + device copy)
 // ---------------------------------------------------------------------------
-struct HostSched {
-  std::vector<Tile> tiles;
-  std::vector<SplitGroup> groups;
-  int total_parts = 0;
-  int tile_nnz = 0, max_rows = 0, e = 8;
-};
 
 // Tiles: runs of whole rows with at most tile_capacity(kBlock, e) nonzeros
 // and at most tile_max_rows(kBlock) rows; a longer row becomes a split group
 // of capacity-sized chunks.
-static HostSched build_sched(const int32_t* rp, int nrows, int e) {
+HostSched build_sched(const int32_t* rp, int nrows, int e, const int64_t* lp_off, int count) {
   HostSched h;
   const int cap = tile_capacity(kBlock, e);
   h.tile_nnz = cap;
   h.max_rows = tile_max_rows(kBlock);
   h.e = e;
+  int lp = 0;
+  int lp_end = lp_off ? (int)lp_off[1] : nrows;
   int r = 0;
+  h.lp_tiles.push_back(0);
   while (r < nrows) {
+    while (lp_off && r >= lp_end && lp + 1 < count) {
+      ++lp;
+      lp_end = (int)lp_off[lp + 1];
+      h.lp_tiles.push_back((int32_t)h.tiles.size());
+    }
     const int64_t len = (int64_t)rp[r + 1] - rp[r];
     if (len > cap) {
       const int nparts = (int)((len + cap - 1) / cap);
@@ -82,7 +74,7 @@ static HostSched build_sched(const int32_t* rp, int nrows, int e) {
       for (int p = 0; p < nparts; ++p) {
         const int64_t b = rp[r] + (int64_t)p * cap;
         const int64_t en = std::min<int64_t>(b + cap, rp[r + 1]);
-        h.tiles.push_back(Tile{r, r + 1, (int32_t)b, (int32_t)en, gid, p, 0, 0});
+        h.tiles.push_back(Tile{r, r + 1, (int32_t)b, (int32_t)en, gid, p, lp, 0});
       }
       h.total_parts += nparts;
       ++r;
@@ -90,108 +82,33 @@ static HostSched build_sched(const int32_t* rp, int nrows, int e) {
     }
     const int start = r;
     int64_t nz = 0;
-    while (r < nrows && r - start < h.max_rows) {
+    while (r < nrows && r < lp_end && r - start < h.max_rows) {
       const int64_t l = (int64_t)rp[r + 1] - rp[r];
       if (l > cap || nz + l > cap) break;
       nz += l;
       ++r;
     }
-    h.tiles.push_back(Tile{start, r, rp[start], rp[r], -1, 0, 0, 0});
+    h.tiles.push_back(Tile{start, r, rp[start], rp[r], -1, 0, lp, 0});
   }
+  // LPs with no rows left (none with m >= 1) still get a range
+  while ((int)h.lp_tiles.size() < count) h.lp_tiles.push_back((int32_t)h.tiles.size());
+  h.lp_tiles.push_back((int32_t)h.tiles.size());
   return h;
 }
 
-struct DevSched {
-  Tile* tiles = nullptr;
-  SplitGroup* groups = nullptr;
-  int32_t* counters = nullptr;
-  double* slots = nullptr;
-  SchedView view{};
-};
-
 }  // namespace pdhg
+
 
 using namespace pdhg;
 
-// ---------------------------------------------------------------------------
-// context
-// ---------------------------------------------------------------------------
-struct pdhg_ctx {
-  int m = 0, n = 0;
-  int64_t nnz = 0, nnz_pad = 0;
-  pdhg_options opt{};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int nsm = 0;
-  size_t smem_optin = 0;
-  bool mixed = false;
-
-  std::vector<void*> allocs;
-  // matrices
-  int32_t *a_rp = nullptr, *a_col = nullptr, *t_rp = nullptr, *t_col = nullptr;
-  double *a_val_orig = nullptr, *t_val_orig = nullptr, *a_val64 = nullptr, *t_val64 = nullptr;
-  float *a_val32 = nullptr, *t_val32 = nullptr;
-  std::vector<int32_t> h_a_rp, h_t_rp;
-  // vectors
-  double *b = nullptr, *c = nullptr, *b_t64 = nullptr, *c_t64 = nullptr, *D_r = nullptr,
-         *D_c = nullptr;
-  float *b_t32 = nullptr, *c_t32 = nullptr;
-  void *x = nullptr, *y = nullptr, *x_avg = nullptr, *y_avg = nullptr, *x_last = nullptr,
-       *y_last = nullptr, *Ax = nullptr, *Ax_avg = nullptr;
-  double *xs64 = nullptr, *ys64 = nullptr, *out_n1 = nullptr, *out_n2 = nullptr,
-         *out_m1 = nullptr, *report = nullptr, *sums = nullptr;
-  Scalars* sc = nullptr;
-  PowerState* ps = nullptr;
-  double* partials = nullptr;  // generic reduction scratch
-  size_t partials_len = 0;
-  double* split_q = nullptr;
-  long long* log_k = nullptr;
-  int32_t* log_flags = nullptr;
-  double* log_kkt = nullptr;
-  int log_cap = 4096;
-  // schedules and launch shapes
-  DevSched sa, st;      // iteration schedules (autotuned nonzeros per thread)
-  DevSched sa8, st8;    // float64 report / Algorithm 1 / power iteration
-  Launch l_prim{}, l_dual{}, l_eval{}, l_a64{}, l_t64{};
-  int restart_grid = 1;
-  // graphs and polling
-  cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
-  cudaEvent_t ev_done[2] = {nullptr, nullptr};
-  cudaEvent_t ev_k[2][4] = {};
-  Scalars* h_sc[2] = {nullptr, nullptr};
-  double timing_sum[2] = {0, 0};
-  long long timing_n = 0;
-  // cached host data
-  double omega0 = 1.0;
-  int power_iters = 0;
-  double report_h[8] = {0};
-  long long launches = 0;  // kernels launched (graph replays count every node)
-  bool report_valid = false;
-  int last_status = PDHG_MAX_ITER;
-};
-
-template <typename T>
-static pdhg_status dalloc(pdhg_ctx* ctx, T** p, size_t count) {
-  void* q = nullptr;
-  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&q, bytes);
-  if (e != cudaSuccess) {
-    set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? PDHG_OOM : PDHG_CUDA_ERROR;
-  }
-  ctx->allocs.push_back(q);
-  *p = static_cast<T*>(q);
-  return PDHG_OK;
-}
-
-static pdhg_status copy_in(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes) {
+pdhg_status pdhg::copy_in(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return PDHG_OK;
   CK(cudaMemcpyAsync(dst, src, bytes,
                      ctx->opt.io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      ctx->stream));
   return PDHG_OK;
 }
-static pdhg_status copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes) {
+pdhg_status pdhg::copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes) {
   if (!dst || bytes == 0) return PDHG_OK;
   CK(cudaMemcpyAsync(dst, src, bytes,
                      ctx->opt.io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -200,13 +117,13 @@ static pdhg_status copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t by
 }
 
 // kind 0: one gathered vector in the iteration precision, 1: two, 2: one in float64
-static size_t smem_for(int kind, bool mixed, int max_rows) {
+size_t pdhg::smem_for(int kind, bool mixed, int max_rows) {
   if (kind == 0) return tile_smem(1, mixed, max_rows);
   if (kind == 1) return tile_smem(2, mixed, max_rows);
   return tile_smem(1, false, max_rows);
 }
 
-static pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) {
+pdhg_status pdhg::upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) {
   *d = DevSched{};
   CKS(dalloc(ctx, &d->tiles, h.tiles.size()));
   CKS(dalloc(ctx, &d->groups, h.groups.size()));
@@ -234,7 +151,7 @@ static pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) 
   return PDHG_OK;
 }
 
-static Launch make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int ntiles) {
+Launch pdhg::make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int ntiles) {
   const int occ = tile_occupancy(occ_kind, e, smem);
   int grid = std::min(ntiles, ctx->nsm * occ);
   return Launch{std::max(grid, 1), smem};
@@ -433,7 +350,7 @@ static pdhg_status build_graphs(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
-static size_t elem(const pdhg_ctx* ctx) { return ctx->mixed ? sizeof(float) : sizeof(double); }
+size_t pdhg::elem(const pdhg_ctx* ctx) { return ctx->mixed ? sizeof(float) : sizeof(double); }
 
 // ---------------------------------------------------------------------------
 // create
@@ -461,9 +378,8 @@ extern "C" void pdhg_default_options(pdhg_options* o) {
   o->verbose = 0;
 }
 
-static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int32_t* col,
-                               const double* val, const double* b, const double* c) {
-  const int m = ctx->m, n = ctx->n;
+// device attributes, stream, kernel shared-memory limits
+pdhg_status pdhg::setup_device(pdhg_ctx* ctx) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -479,29 +395,14 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
   CK(configure_tile_kernels(ctx->smem_optin));
   CK(configure_setup_kernels(ctx->smem_optin));
 
-  // row pointer on the host (scheduler) and its checks
-  ctx->h_a_rp.resize((size_t)m + 1);
-  if (ctx->opt.io_on_device) {
-    CK(cudaMemcpyAsync(ctx->h_a_rp.data(), row_ptr, sizeof(int32_t) * (m + 1),
-                       cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-  } else {
-    std::memcpy(ctx->h_a_rp.data(), row_ptr, sizeof(int32_t) * (m + 1));
-  }
-  if (ctx->h_a_rp[0] != 0) {
-    set_error("row_ptr[0] must be 0");
-    return PDHG_INVALID_ARG;
-  }
-  for (int i = 0; i < m; ++i)
-    if (ctx->h_a_rp[i + 1] < ctx->h_a_rp[i]) {
-      set_error("row_ptr decreases at row %d", i);
-      return PDHG_INVALID_ARG;
-    }
-  ctx->nnz = ctx->h_a_rp[m];
-  ctx->nnz_pad = (ctx->nnz + 7) / 4 * 4 + 4;
-  const int64_t nnz = ctx->nnz, np = ctx->nnz_pad;
+  return PDHG_OK;
+}
 
-  // device arrays
+// every device array of the context (sizes m, n, nnz and count set)
+pdhg_status pdhg::alloc_arrays(pdhg_ctx* ctx) {
+  const int m = ctx->m, n = ctx->n;
+  ctx->nnz_pad = (ctx->nnz + 7) / 4 * 4 + 4;
+  const int64_t np = ctx->nnz_pad;
   CKS(dalloc(ctx, &ctx->a_rp, (size_t)m + 1));
   CKS(dalloc(ctx, &ctx->t_rp, (size_t)n + 1));
   CKS(dalloc(ctx, &ctx->a_col, np));
@@ -534,17 +435,20 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
   CKS(dalloc(ctx, &ctx->out_m1, m));
   CKS(dalloc(ctx, &ctx->report, 8));
   CKS(dalloc(ctx, &ctx->sums, 8));
-  CKS(dalloc(ctx, &ctx->sc, 1));
-  CKS(dalloc(ctx, &ctx->ps, 1));
+  CKS(dalloc(ctx, &ctx->sc, (size_t)ctx->count));
+  CKS(dalloc(ctx, &ctx->ps, (size_t)ctx->count));
   CKS(dalloc(ctx, &ctx->log_k, ctx->log_cap));
   CKS(dalloc(ctx, &ctx->log_flags, ctx->log_cap));
   CKS(dalloc(ctx, &ctx->log_kkt, 3 * (size_t)ctx->log_cap));
-  int32_t* flags = nullptr;
-  int32_t *cnt = nullptr, *tmp = nullptr;
-  CKS(dalloc(ctx, &flags, 1));
-  CKS(dalloc(ctx, &cnt, (size_t)n + 1));
-  CKS(dalloc(ctx, &tmp, (size_t)n / 1024 + 8));
 
+  return PDHG_OK;
+}
+
+// A (row pointer from ctx->h_a_rp), b, c onto the device
+pdhg_status pdhg::upload_lp(pdhg_ctx* ctx, const int32_t* col, const double* val, const double* b,
+                            const double* c) {
+  const int m = ctx->m, n = ctx->n;
+  const int64_t nnz = ctx->nnz, np = ctx->nnz_pad;
   CK(cudaMemsetAsync(ctx->a_col, 0, sizeof(int32_t) * np, ctx->stream));
   CK(cudaMemsetAsync(ctx->t_col, 0, sizeof(int32_t) * np, ctx->stream));
   CK(cudaMemsetAsync(ctx->a_val_orig, 0, sizeof(double) * np, ctx->stream));
@@ -562,6 +466,21 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
   CKS(copy_in(ctx, ctx->b, b, sizeof(double) * m));
   CKS(copy_in(ctx, ctx->c, c, sizeof(double) * n));
 
+  return PDHG_OK;
+}
+
+// validation, a1 transpose, a2 scaling, scaled copies, zero iterate
+pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
+  const int m = ctx->m, n = ctx->n;
+  const int64_t nnz = ctx->nnz, np = ctx->nnz_pad;
+  const size_t es = elem(ctx);
+  void** vecs_n[] = {&ctx->x, &ctx->x_avg, &ctx->x_last};
+  void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg};
+  int32_t* flags = nullptr;
+  int32_t *cnt = nullptr, *tmp = nullptr;
+  CKS(dalloc(ctx, &flags, 1));
+  CKS(dalloc(ctx, &cnt, (size_t)n + 1));
+  CKS(dalloc(ctx, &tmp, (size_t)n / 1024 + 8));
   // validation on device
   CK(cudaMemsetAsync(flags, 0, sizeof(int32_t), ctx->stream));
   launch_validate(m, n, ctx->a_rp, ctx->a_col, ctx->a_val_orig, ctx->b, ctx->c, flags, ctx->stream);
@@ -636,6 +555,37 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
   for (void** p : vecs_n) CK(cudaMemsetAsync(*p, 0, es * n, ctx->stream));
   for (void** p : vecs_m) CK(cudaMemsetAsync(*p, 0, es * m, ctx->stream));
 
+  return PDHG_OK;
+}
+
+static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int32_t* col,
+                               const double* val, const double* b, const double* c) {
+  const int m = ctx->m, n = ctx->n;
+  CKS(setup_device(ctx));
+  // row pointer on the host (scheduler) and its checks
+  ctx->h_a_rp.resize((size_t)m + 1);
+  if (ctx->opt.io_on_device) {
+    CK(cudaMemcpyAsync(ctx->h_a_rp.data(), row_ptr, sizeof(int32_t) * (m + 1),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::memcpy(ctx->h_a_rp.data(), row_ptr, sizeof(int32_t) * (m + 1));
+  }
+  if (ctx->h_a_rp[0] != 0) {
+    set_error("row_ptr[0] must be 0");
+    return PDHG_INVALID_ARG;
+  }
+  for (int i = 0; i < m; ++i)
+    if (ctx->h_a_rp[i + 1] < ctx->h_a_rp[i]) {
+      set_error("row_ptr decreases at row %d", i);
+      return PDHG_INVALID_ARG;
+    }
+  ctx->nnz = ctx->h_a_rp[m];
+
+  CKS(alloc_arrays(ctx));
+  CKS(upload_lp(ctx, col, val, b, c));
+  CKS(prepare_matrix(ctx));
+
   // tile schedules
   CKS(choose_schedules(ctx));
 
@@ -691,7 +641,12 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     ctx->power_iters = hp.k;
   }
 
-  // polling / timing resources
+  CKS(polling_resources(ctx));
+  return PDHG_OK;
+}
+
+// events and pinned status copies of the chunked solve loop
+pdhg_status pdhg::polling_resources(pdhg_ctx* ctx) {
   for (int g = 0; g < 2; ++g) {
     CK(cudaEventCreateWithFlags(&ctx->ev_done[g], cudaEventDisableTiming));
     CK(cudaMallocHost((void**)&ctx->h_sc[g], sizeof(Scalars)));
@@ -772,7 +727,11 @@ extern "C" pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_ite
   if (!ctx) {
     set_error("ctx is NULL");
     return PDHG_INVALID_ARG;
+  }  if (ctx->batch) {
+    set_error("this entry point takes a single-LP context; use the pdhg_batch_* calls");
+    return PDHG_INVALID_ARG;
   }
+
   if (!(eps_rel >= 0.0) || max_iter < 0) {
     set_error("need eps_rel >= 0 and max_iter >= 0");
     return PDHG_INVALID_ARG;
@@ -904,7 +863,11 @@ extern "C" pdhg_status pdhg_get(pdhg_ctx* ctx, double* x, double* y, double* z, 
   if (!ctx) {
     set_error("ctx is NULL");
     return PDHG_INVALID_ARG;
+  }  if (ctx->batch) {
+    set_error("this entry point takes a single-LP context; use the pdhg_batch_* calls");
+    return PDHG_INVALID_ARG;
   }
+
   CKS(compute_report(ctx));
   CKS(copy_out(ctx, x, ctx->out_n1, sizeof(double) * ctx->n));
   CKS(copy_out(ctx, z, ctx->out_n2, sizeof(double) * ctx->n));
@@ -945,7 +908,11 @@ extern "C" pdhg_status pdhg_warmstart_point(pdhg_ctx* ctx, double mu_min, double
   if (!ctx) {
     set_error("ctx is NULL");
     return PDHG_INVALID_ARG;
+  }  if (ctx->batch) {
+    set_error("this entry point takes a single-LP context; use the pdhg_batch_* calls");
+    return PDHG_INVALID_ARG;
   }
+
   if (!(mu_min > 0.0) || !(delta_max >= 0.0) || !(alpha_min > 0.0)) {
     set_error("need mu_min > 0, delta_max >= 0, alpha_min > 0");
     return PDHG_INVALID_ARG;
@@ -1039,7 +1006,11 @@ extern "C" pdhg_status pdhg_get_state(pdhg_ctx* ctx, double* x, double* y, doubl
   if (!ctx) {
     set_error("ctx is NULL");
     return PDHG_INVALID_ARG;
+  }  if (ctx->batch) {
+    set_error("this entry point takes a single-LP context; use the pdhg_batch_* calls");
+    return PDHG_INVALID_ARG;
   }
+
   const int n = ctx->n, m = ctx->m;
   CKS(state_out(ctx, x, ctx->x, n));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1076,7 +1047,11 @@ extern "C" pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const doub
   if (!ctx || !x || !y || !x_avg || !y_avg || !x_last || !y_last || !scalars) {
     set_error("pdhg_set_state needs every argument");
     return PDHG_INVALID_ARG;
+  }  if (ctx->batch) {
+    set_error("this entry point takes a single-LP context; use the pdhg_batch_* calls");
+    return PDHG_INVALID_ARG;
   }
+
   const int n = ctx->n, m = ctx->m;
   CKS(state_in(ctx, ctx->x, x, n));
   CKS(state_in(ctx, ctx->x_avg, x_avg, n));

@@ -48,6 +48,23 @@ __host__ __device__ constexpr size_t tile_smem_bytes(int max_rows) {
 // Epilogue concept:  __device__ void row(int r, const T (&s)[NV], int split_group)
 // split_group < 0 for rows completed inside one tile; otherwise the index of
 // the split group whose last chunk is finishing the row.
+// Optional, called by every thread of the block:
+//   __device__ bool begin_tile(const Tile&)   false skips the tile
+//   __device__ void end_tile(const Tile&, int tile_index)
+template <class Epi>
+__device__ __forceinline__ auto epi_begin(Epi& e, const Tile& t, int) -> decltype(e.begin_tile(t)) {
+  return e.begin_tile(t);
+}
+template <class Epi>
+__device__ __forceinline__ bool epi_begin(Epi&, const Tile&, long) {
+  return true;
+}
+template <class Epi>
+__device__ __forceinline__ auto epi_end(Epi& e, const Tile& t, int i, int) -> decltype(e.end_tile(t, i)) {
+  e.end_tile(t, i);
+}
+template <class Epi>
+__device__ __forceinline__ void epi_end(Epi&, const Tile&, int, long) {}
 template <typename T, int NV, int BLOCK, int E, class Epi>
 __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __restrict__ row_ptr,
                                           const int32_t* __restrict__ col,
@@ -65,6 +82,7 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
 
   for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
     const Tile tl = S.tiles[t];
+    if (!epi_begin(epi, tl, 0)) continue;
     const int nzb = tl.nz_begin, nze = tl.nz_end;
     const int w0 = (nzb & ~3) + tid * E;
 
@@ -139,6 +157,7 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
         }
       }
       __syncthreads();
+      epi_end(epi, tl, t, 0);
       continue;
     }
 
@@ -254,6 +273,7 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
       epi.row(tl.row_begin + r, s, -1);
     }
     __syncthreads();
+    epi_end(epi, tl, t, 0);
   }
 }
 

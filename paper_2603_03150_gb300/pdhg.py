@@ -83,6 +83,10 @@ _SIGS = {
     "pdhg_get_kernel_timing": (_I32, [_P, _P, _P, _P]),
     "pdhg_get_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "pdhg_get_launch_count": (_I32, [_P, _P]),
+    "pdhg_batch_create": (_I32, [_PP, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
+    "pdhg_batch_solve": (_I32, [_P, _D, _I64, _P]),
+    "pdhg_batch_get": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "pdhg_batch_warmstart_point": (_I32, [_P, _D, _D, _D, _I32, _P, _P, _P, _P]),
     "pdhg_centered_point_noalloc": (_I32, [_I32, _P, _P, _D, _D, _D, _P, _P, _P, _P]),
     "pdhg_destroy": (None, [_P]),
     "pdhg_last_error": (ctypes.c_char_p, []),
@@ -322,3 +326,84 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class BatchSolver(Solver):
+    """Many LPs solved together (block-diagonal batch with per-LP state).
+
+    ``lps`` is a list of objects with m, n, row_ptr, col, val, b, c (e.g.
+    lpgen.LP); or pass the concatenated arrays via ``arrays=`` (dict with
+    m, n, row_ptr, col, val, b, c as the C ABI takes them)."""
+
+    def __init__(self, lps=None, arrays=None, precision: str = "fp64", eval_freq: int = 64,
+                 device_io: bool = False, stream=None, use_graphs: bool = True, **kw):
+        L = lib()
+        o = Options()
+        L.pdhg_default_options(ctypes.byref(o))
+        o.precision = FP32_MIXED if precision in ("fp32", "fp32_mixed", "mixed") else FP64
+        o.eval_freq = eval_freq
+        o.io_on_device = 1 if device_io else 0
+        o.stream = stream
+        o.use_graphs = 1 if use_graphs else 0
+        for k, v in kw.items():
+            setattr(o, k, v)
+        if arrays is None:
+            arrays = dict(
+                m=np.array([lp.m for lp in lps], dtype=np.int32),
+                n=np.array([lp.n for lp in lps], dtype=np.int32),
+                row_ptr=np.concatenate([np.asarray(lp.row_ptr, np.int32) for lp in lps]),
+                col=np.concatenate([np.asarray(lp.col, np.int32) for lp in lps]),
+                val=np.concatenate([np.asarray(lp.val, np.float64) for lp in lps]),
+                b=np.concatenate([np.asarray(lp.b, np.float64) for lp in lps]),
+                c=np.concatenate([np.asarray(lp.c, np.float64) for lp in lps]))
+        self.ms = np.ascontiguousarray(arrays["m"], dtype=np.int32)
+        self.ns = np.ascontiguousarray(arrays["n"], dtype=np.int32)
+        self.count = int(self.ms.size)
+        self.m, self.n = int(self.ms.sum()), int(self.ns.sum())
+        self.device_io = device_io
+        self.mixed = o.precision == FP32_MIXED
+        a = dict(arrays)
+        if not device_io:
+            for k, dt in [("row_ptr", np.int32), ("col", np.int32), ("val", np.float64),
+                          ("b", np.float64), ("c", np.float64)]:
+                if not _is_torch(a[k]):
+                    a[k] = np.ascontiguousarray(a[k], dtype=dt)
+        self._keep = a
+        self._ctx = ctypes.c_void_p()
+        self._L = L
+        st = L.pdhg_batch_create(ctypes.byref(self._ctx), self.count, _ptr(self.ms), _ptr(self.ns),
+                                 _ptr(a["row_ptr"]), _ptr(a["col"]), _ptr(a["val"]), _ptr(a["b"]),
+                                 _ptr(a["c"]), ctypes.byref(o))
+        _check(st, allow_positive=False)
+        self.status = None
+        self.m_off = np.concatenate([[0], np.cumsum(self.ms)]).astype(np.int64)
+        self.n_off = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
+
+    def solve(self, eps_rel: float = 1e-4, max_iter: int = 1_000_000):
+        st = np.zeros(self.count, dtype=np.int32)
+        self.status = _check(self._L.pdhg_batch_solve(self._ctx, eps_rel, max_iter, _ptr(st)))
+        self.lp_status = st
+        return self.status
+
+    def get(self, out=None):
+        x, y, z = out if out is not None else (self._new(self.n), self._new(self.m), self._new(self.n))
+        arr = [np.zeros(self.count) for _ in range(4)]
+        it = np.zeros(self.count, dtype=np.int64)
+        _check(self._L.pdhg_batch_get(self._ctx, _ptr(x), _ptr(y), _ptr(z), *[_ptr(q) for q in arr],
+                                      _ptr(it)))
+        return dict(x=x, y=y, z=z, r_P=arr[0], r_D=arr[1], gap=arr[2], max_violation=arr[3],
+                    iters=it)
+
+    def warmstart_point(self, mu_min: float = 1e-6, delta_max: float = 1e-4,
+                        alpha_min: float = 1e-6, unscaled: bool = False, out=None):
+        x, y, z = out if out is not None else (self._new(self.n), self._new(self.m), self._new(self.n))
+        mu = np.zeros(self.count)
+        _check(self._L.pdhg_batch_warmstart_point(self._ctx, mu_min, delta_max, alpha_min,
+                                                  1 if unscaled else 0, _ptr(x), _ptr(y), _ptr(z),
+                                                  _ptr(mu)))
+        return x, y, z, mu
+
+    def split(self, v, side: str):
+        """Per-LP pieces of a concatenated vector ('n' or 'm' side)."""
+        off = self.n_off if side == "n" else self.m_off
+        return [v[off[i]:off[i + 1]] for i in range(self.count)]
