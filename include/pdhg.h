@@ -206,6 +206,29 @@ pdhg_status pdhg_batch_warmstart_point(pdhg_ctx* ctx, double mu_min, double delt
                                        double alpha_min, int32_t unscaled, double* x_ws,
                                        double* y_ws, double* z_ws, double* lp_mu);
 
+/* ---- differentiation through the converged batch solution ---------------
+ * At a PDHG fixed point x = max(0, x - tau (c - A^T y)), the set
+ * B = {j : x_j - tau (c - A^T y)_j > 0} gives A_B x_B = b, x_j = 0 off B.
+ * pdhg_batch_polish fixes B from each LP's returned iterate (scaled model)
+ * and replaces x_B by the least-squares solution of A_B x_B = b (conjugate
+ * gradients on the scaled normal equations, warm-started at the PDHG
+ * iterate, stopping at relative residual cg_tol or cg_max_iter steps).
+ *  x            float64[sum n] polished x in the original models (or NULL)
+ *  lp_active    HOST int32[count]: |B| per LP (or NULL)
+ *  lp_cg_iters  HOST int32[count]: CG steps per LP (or NULL)  */
+pdhg_status pdhg_batch_polish(pdhg_ctx* ctx, double cg_tol, int32_t cg_max_iter, double* x,
+                              int32_t* lp_active, int32_t* lp_cg_iters);
+
+/* Vector-Jacobian product through x*(b, c) with B fixed by pdhg_batch_polish:
+ * given grad_x = dL/dx (float64[sum n]) returns
+ *   grad_b = A_B (A_B^T A_B)^{-1} grad_x_B   (float64[sum m], per LP)
+ *   grad_c = 0                               (float64[sum n], or NULL)
+ * (x_B does not move with c while B is fixed).  Requires a prior
+ * pdhg_batch_polish; otherwise PDHG_INVALID_ARG.  */
+pdhg_status pdhg_batch_adjoint(pdhg_ctx* ctx, const double* grad_x, double* grad_b,
+                               double* grad_c, double cg_tol, int32_t cg_max_iter,
+                               int32_t* lp_cg_iters);
+
 /* Algorithm 1's centered start point (as pdhg_warmstart_point, scaled
  * output) for caller-provided DEVICE vectors, allocating no device memory.
  * The paper has no counterpart of this entry point: it exists for callers

@@ -1131,6 +1131,8 @@ static pdhg_status batch_returned64(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
+pdhg_status batch_returned64_adj(pdhg_ctx* ctx) { return batch_returned64(ctx); }
+
 extern "C" pdhg_status pdhg_batch_get(pdhg_ctx* ctx, double* x, double* y, double* z,
                                       double* lp_r_P, double* lp_r_D, double* lp_gap,
                                       double* lp_max_violation, int64_t* lp_iters) {

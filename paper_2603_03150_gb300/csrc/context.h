@@ -58,6 +58,9 @@ struct DevSched {
 
 }  // namespace pdhg
 
+struct pdhg_ctx;
+void pdhg_free_adjoint(pdhg_ctx* ctx);
+
 using pdhg::DevSched;
 using pdhg::Launch;
 using pdhg::PowerState;
@@ -105,6 +108,7 @@ struct pdhg_ctx {
   double *rec_t = nullptr, *rec_a = nullptr;  // per-tile evaluation / report records
   int32_t* active = nullptr;                  // LPs not finished after the last evaluation
   double* breport = nullptr;                  // [count][8] per-LP report
+  void* adjoint = nullptr;                    // active-set polish / adjoint buffers
   // schedules and launch shapes
   DevSched sa, st;      // iteration schedules (autotuned nonzeros per thread)
   DevSched sa8, st8;    // float64 report / Algorithm 1 / power iteration

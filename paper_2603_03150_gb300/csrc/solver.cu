@@ -714,6 +714,7 @@ extern "C" void pdhg_destroy(pdhg_ctx* ctx) {
     for (int e = 0; e < 4; ++e)
       if (ctx->ev_k[g][e]) cudaEventDestroy(ctx->ev_k[g][e]);
   }
+  pdhg_free_adjoint(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

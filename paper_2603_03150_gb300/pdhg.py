@@ -87,6 +87,8 @@ _SIGS = {
     "pdhg_batch_solve": (_I32, [_P, _D, _I64, _P]),
     "pdhg_batch_get": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pdhg_batch_warmstart_point": (_I32, [_P, _D, _D, _D, _I32, _P, _P, _P, _P]),
+    "pdhg_batch_polish": (_I32, [_P, _D, _I32, _P, _P, _P]),
+    "pdhg_batch_adjoint": (_I32, [_P, _P, _P, _P, _D, _I32, _P]),
     "pdhg_centered_point_noalloc": (_I32, [_I32, _P, _P, _D, _D, _D, _P, _P, _P, _P]),
     "pdhg_destroy": (None, [_P]),
     "pdhg_last_error": (ctypes.c_char_p, []),
@@ -407,3 +409,22 @@ class BatchSolver(Solver):
         """Per-LP pieces of a concatenated vector ('n' or 'm' side)."""
         off = self.n_off if side == "n" else self.m_off
         return [v[off[i]:off[i + 1]] for i in range(self.count)]
+
+    def polish(self, cg_tol: float = 1e-12, cg_max_iter: int = 5000, out=None):
+        """Fix the active set B and solve A_B x_B = b in least squares (per LP)."""
+        x = out if out is not None else self._new(self.n)
+        act = np.zeros(self.count, dtype=np.int32)
+        it = np.zeros(self.count, dtype=np.int32)
+        _check(self._L.pdhg_batch_polish(self._ctx, cg_tol, cg_max_iter, _ptr(x), _ptr(act),
+                                         _ptr(it)))
+        return dict(x=x, active=act, cg_iters=it)
+
+    def adjoint(self, grad_x, cg_tol: float = 1e-12, cg_max_iter: int = 5000, out=None):
+        """dL/db and dL/dc from dL/dx through the polished solution."""
+        gb, gc = out if out is not None else (self._new(self.m), self._new(self.n))
+        it = np.zeros(self.count, dtype=np.int32)
+        if not self.device_io and not _is_torch(grad_x):
+            grad_x = np.ascontiguousarray(grad_x, dtype=np.float64)
+        _check(self._L.pdhg_batch_adjoint(self._ctx, _ptr(grad_x), _ptr(gb), _ptr(gc), cg_tol,
+                                          cg_max_iter, _ptr(it)))
+        return dict(grad_b=gb, grad_c=gc, cg_iters=it)
