@@ -38,6 +38,10 @@ WORKLOADS = {
     "transport": ("balanced transportation LP 2000 supply x 2000 demand, m=4000 "
                   "n=4000000 nnz=8000000, seed 0"),
     "small": "planted LP m=200 n=500, 5 nnz per column, seed 0",
+    "batch": ("512 planted LPs, m ~ floor(exp(U[ln 50, ln 5000])) (seed 0), n = floor(2.5 m), "
+              "5 nnz per column, LP i seeded i (sum m=617840, sum n=1544469, sum nnz=7722345)"),
+    "adjoint": ("64 planted LPs m=2000 n=5000, 5 nnz per column, seeds 0..63, targets "
+                "U[0,1] seeded 1000+i; loss ||x - x_target||^2"),
 }
 
 
@@ -51,6 +55,30 @@ def make_lp(name):
 
 
 # ---------------------------------------------------------------------------
+def shard_lps(weights, world_size):
+    """Greedy balance of independent LPs over ranks by weight (nonzeros),
+    heaviest first; returns sorted index lists, one per rank."""
+    order = sorted(range(len(weights)), key=lambda i: (-weights[i], i))
+    load = [0] * world_size
+    parts = [[] for _ in range(world_size)]
+    for i in order:
+        r = min(range(world_size), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += weights[i]
+    return [sorted(p) for p in parts]
+
+
+def reduce_over_ranks(total_ms, units, device):
+    """Max of the timed milliseconds and sum of the work units over ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -228,11 +256,7 @@ def run_ours(args):
     total_ms = sum(r["ms"] for r in rec)
     total_it = sum(r["iters"] for r in rec)
     if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        it = torch.tensor([total_it], dtype=torch.float64, device=dev)
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        total_ms, total_it_all = float(t.item()), float(it.item())
+        total_ms, total_it_all = reduce_over_ranks(total_ms, total_it, dev)
     else:
         total_it_all = float(total_it)
     value = total_it_all / (total_ms / 1e3)
@@ -315,6 +339,132 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Batched solve of the 512-LP workload (FP32-mixed and FP64) against 512
+    sequential FP64 single-LP solves on the same GPU.  Ranks take disjoint
+    shards of the LPs (no collective on the data path)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_03150_gb300 import build as B
+    from paper_2603_03150_gb300 import lpgen, pdhg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+    all_lps = lpgen.planted_batch(512)
+    mine = shard_lps([lp.nnz for lp in all_lps], ws)[rank]
+    lps = [all_lps[i] for i in mine]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    def batched(precision):
+        s = pdhg.BatchSolver(lps, precision=precision)
+        st = s.solve(EPS, args.max_iter)
+        g = s.get()
+        s.close()
+        return st, g
+
+    res = {}
+    for prec in ("fp32", "fp64"):
+        for _ in range(max(1, args.warmup - 2)):
+            batched(prec)
+        ms = []
+        for _ in range(args.steps):
+            t, (st, g) = timed(lambda: batched(prec))
+            ms.append(t)
+        res[prec] = dict(ms=float(np.mean(ms)), status=int(st),
+                         iters_max=int(g["iters"].max()), iters_median=int(np.median(g["iters"])),
+                         max_violation_max=float(g["max_violation"].max()))
+
+    def sequential():
+        it = []
+        for lp in lps:
+            with pdhg.Solver.from_lp(lp) as s1:
+                s1.solve(EPS, args.max_iter)
+                s1.get()
+                it.append(s1.info(violation=False)["iters"])
+        return it
+
+    t_seq, seq_it = timed(sequential)
+    total_ms = res["fp32"]["ms"]
+    units = len(lps)
+    if ws > 1:
+        total_ms, units = reduce_over_ranks(total_ms, units, dev)
+    if rank == 0:
+        line = {"metric": "LPs solved to eps_rel=1e-4 per second (batched, FP32-mixed)",
+                "value": round(units / (total_ms / 1e3), 2), "unit": "LP/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms, 2),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": {"workload": WORKLOADS["batch"], "eps_rel": EPS,
+                                                "step": "batch create + solve + get",
+                                                "parallelism": f"LP shards x{ws}"},
+                "batched_fp32": res["fp32"], "batched_fp64": res["fp64"],
+                "sequential_fp64_ms": round(t_seq, 2),
+                "sequential_fp64_iters_median": int(np.median(seq_it)),
+                "batched_fp64_vs_sequential_fp64_speedup": round(t_seq / res["fp64"]["ms"], 2),
+                "batched_fp32_vs_sequential_fp64_speedup": round(t_seq / res["fp32"]["ms"], 2)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_adjoint(args):
+    """64 LPs of 2000 x 5000: batched solve + active-set polish + adjoint."""
+    import torch
+
+    from oracle import adjoint_ref as R
+    from paper_2603_03150_gb300 import build as B
+    from paper_2603_03150_gb300 import lpgen, pdhg
+
+    B.build()
+    lps, targets = lpgen.adjoint_batch(64, 2000, 5000)
+    tcat = np.concatenate(targets)
+
+    def step():
+        s = pdhg.BatchSolver(lps)
+        s.solve(EPS, args.max_iter)
+        p = s.polish()
+        a = s.adjoint(2.0 * (p["x"] - tcat))
+        s.close()
+        return p, a
+
+    for _ in range(max(1, args.warmup - 2)):
+        step()
+    ms = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p, a = step()
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+    ms_step = float(np.mean(ms))
+    lp = lps[0]
+    Bset = lp.x_star > 0
+    A = lp.dense()
+    gr = R.grad_b(A, Bset, 2.0 * (R.polish(A, lp.b, Bset) - targets[0]))
+    err = float(np.linalg.norm(a["grad_b"][:lp.m] - gr) / np.linalg.norm(gr))
+    line = {"metric": "gradients dL/db, dL/dc per second (64 LPs, batched solve + polish + adjoint)",
+            "value": round(64 / (ms_step / 1e3), 2), "unit": "LP-gradients/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS["adjoint"], "eps_rel": EPS},
+            "grad_b_rel_err_vs_dense_lp0": err, "active_set_sizes": sorted(set(p["active"].tolist())),
+            "cg_iters_max": int(a["cg_iters"].max())}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(lp, iters):
     """The oracle as it stands, timed on this host: its set-up once (timed
     apart), then `iters` PDHG iterations (steady-state iterations per second)."""
@@ -390,6 +540,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
