@@ -72,7 +72,10 @@ typedef struct pdhg_options {
   int32_t use_graphs;      /* 1 (default): replay each F-iteration chunk as a
                               CUDA graph                                        */
   int32_t autotune;        /* 1 (default): time SpMV tile schedules at create   */
-  int32_t tile_nnz;        /* >0: fixed nonzeros per SpMV tile (no autotune)    */
+  int32_t tile_nnz;        /* 0: autotune; > 0: segmented SpMV tiles of about
+                              this many nonzeros; -4 / -8: the vector SpMV with
+                              4 / 8 lanes per row (matrices whose rows all have
+                              <= 256 nonzeros; others fall back to segmented)  */
   int32_t kernel_timing;   /* 1: sample primal/dual kernel durations with CUDA
                               events during pdhg_solve                          */
   int32_t verbose;
@@ -207,10 +210,10 @@ pdhg_status pdhg_batch_warmstart_point(pdhg_ctx* ctx, double mu_min, double delt
                                        double* y_ws, double* z_ws, double* lp_mu);
 
 /* ---- differentiation through the converged batch solution ---------------
- * At a PDHG fixed point x = max(0, x - tau (c - A^T y)), the set
- * B = {j : x_j - tau (c - A^T y)_j > 0} gives A_B x_B = b, x_j = 0 off B.
- * pdhg_batch_polish fixes B from each LP's returned iterate (scaled model)
- * and replaces x_B by the least-squares solution of A_B x_B = b (conjugate
+ * At a PDHG fixed point x = max(0, x - tau (c - A^T y)) the positive set B
+ * gives A_B x_B = b, x_j = 0 off B.  pdhg_batch_polish predicts B from each
+ * LP's returned iterate by complementarity in the scaled model,
+ * B = {j : x~_j > z~_j} with z~ = max(0, c~ - A~^T y~), and replaces x_B by the least-squares solution of A_B x_B = b (conjugate
  * gradients on the scaled normal equations, warm-started at the PDHG
  * iterate, stopping at relative residual cg_tol or cg_max_iter steps).
  *  x            float64[sum n] polished x in the original models (or NULL)

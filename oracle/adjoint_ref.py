@@ -2,8 +2,10 @@
 
 TEST INFRASTRUCTURE (tests only).  Plain numpy on dense matrices.
 
-At a PDHG fixed point x = max(0, x - tau (c - A^T y)), the positive set
-B = {j : x_j - tau (c - A^T y)_j > 0} satisfies A_B x_B = b, x_j = 0 off B.
+At a PDHG fixed point x = max(0, x - tau (c - A^T y)) the positive set B
+satisfies A_B x_B = b, x_j = 0 off B.  From an approximate iterate it is
+predicted by complementarity in the scaled model: B = {j : x~_j > z~_j} with
+z~ = max(0, c~ - A~^T y~).
 With B fixed: x_B = least-squares solution of A_B x_B = b (exact, b is in
 the range), and for a loss L(x) with g = dL/dx the min-norm active-set
 Jacobian gives dL/db = A_B (A_B^T A_B)^{-1} g_B -- the minimum-norm u with
@@ -16,10 +18,9 @@ from . import pdhg_oracle as O
 
 def active_set(res: "O.Result") -> np.ndarray:
     """B from the oracle's returned iterate in the scaled model."""
-    S, st = res.setup, res.state
-    tau = S.eta / st.omega
-    xs, ys = res.x_scaled, res.y_scaled
-    return xs - tau * (S.c_t - S.At.T @ ys) > 0.0
+    S = res.setup
+    zs = np.maximum(0.0, S.c_t - S.At.T @ res.y_scaled)
+    return res.x_scaled > zs
 
 
 def polish(A: np.ndarray, b: np.ndarray, B: np.ndarray) -> np.ndarray:

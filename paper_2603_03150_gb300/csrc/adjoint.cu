@@ -1,10 +1,12 @@
 // Differentiation through the converged batch solution by the active-set
 // fixed point of the projected primal step.
 //
-// At a PDHG fixed point x = max(0, x - tau (c - A^T y)); the set
-// B = {j : x_j - tau (c - A^T y)_j > 0} of positive entries satisfies
-// A_B x_B = b and x_j = 0 off B, so (with B fixed) x_B is the least-squares
-// solution of A_B x_B = b and does not move with c.  For a loss L(x):
+// At a PDHG fixed point x = max(0, x - tau (c - A^T y)) the positive
+// entries B satisfy A_B x_B = b and x_j = 0 off B, so (with B fixed) x_B is
+// the least-squares solution of A_B x_B = b and does not move with c.  From an
+// approximate iterate (possibly the running average) B is predicted by
+// complementarity in the scaled model: B = {j : x~_j > z~_j}, z~ =
+// max(0, c~ - A~^T y~).  For a loss L(x):
 //   dL/db = A_B (A_B^T A_B)^{-1} g_B,  g = dL/dx,   dL/dc = 0.
 // The polish solves A_B x_B = b (consistent, so any row weighting gives the
 // same x_B) in the scaled model, which is better conditioned: CG on
@@ -25,20 +27,19 @@ struct CgState {
   int32_t iters, max_iter, done, pad;
 };
 
-// mask of B and its size per LP: z~ = c~ - A~^T y~ gathered through the tiles
+// mask of B = {j : x~_j > z~_j} and its size per LP (z~ through the tiles)
 template <int BLOCK>
 struct MaskEpi {
   const double *x_s, *c_t;
   const Scalars* sc;
   double *mask, *rec, *red;
-  double cnt, tau;
-  __device__ __forceinline__ bool begin_tile(const Tile& tl) {
+  double cnt, unused;
+  __device__ __forceinline__ bool begin_tile(const Tile&) {
     cnt = 0.0;
-    tau = sc[tl.lp].tau;
     return true;
   }
   __device__ __forceinline__ void row(int j, const double (&s)[1], int) {
-    const bool in = x_s[j] - tau * (c_t[j] - s[0]) > 0.0;
+    const bool in = x_s[j] > fmax(0.0, c_t[j] - s[0]);
     mask[j] = in ? 1.0 : 0.0;
     cnt += in ? 1.0 : 0.0;
   }

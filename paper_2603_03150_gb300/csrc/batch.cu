@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(BLOCK) k_bprimal(BatchBuffers<T> B, int i) {
   extern __shared__ __align__(16) unsigned char smem[];
   BPrimalEpi<T> epi{B.it.x, B.it.c_t, B.it.x_avg, B.it.sc, i, T(0), T(0), false};
   Gather<T, 1> g{{B.it.y}};
-  run_tiles<T, 1, BLOCK, E>(B.it.t_sched, B.it.t_rp, B.it.t_col, B.it.t_val, g, epi, smem);
+  run_sched<T, 1, BLOCK, E>(B.it.t_sched, B.it.t_rp, B.it.t_col, B.it.t_val, g, epi, smem);
 }
 
 template <typename T, int BLOCK, int E>
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(BLOCK) k_bdual(BatchBuffers<T> B, int i) {
   extern __shared__ __align__(16) unsigned char smem[];
   BDualEpi<T> epi{B.it.y, B.it.b_t, B.it.Ax, B.it.y_avg, B.it.Ax_avg, B.it.sc, i, T(0), T(0), false};
   Gather<T, 1> g{{B.it.x}};
-  run_tiles<T, 1, BLOCK, E>(B.it.a_sched, B.it.a_rp, B.it.a_col, B.it.a_val, g, epi, smem);
+  run_sched<T, 1, BLOCK, E>(B.it.a_sched, B.it.a_rp, B.it.a_col, B.it.a_val, g, epi, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(BLOCK) k_beval(BatchBuffers<T> B, int chunk) {
   const IterBuffers<T>& I = B.it;
   BEvalEpi<T, BLOCK> epi{I.x, I.x_avg, I.x_last, I.c_t64, I.D_c, I.sc, B.rec_t, red, {}};
   Gather<T, 2> g{{I.y, I.y_avg}};
-  run_tiles<T, 2, BLOCK, E>(I.t_sched, I.t_rp, I.t_col, I.t_val, g, epi, smem);
+  run_sched<T, 2, BLOCK, E>(I.t_sched, I.t_rp, I.t_col, I.t_val, g, epi, smem);
   // m side over the row ranges of A's tiles (no products needed)
   for (int t = blockIdx.x; t < I.a_sched.ntiles; t += gridDim.x) {
     const Tile tl = I.a_sched.tiles[t];
@@ -674,6 +674,14 @@ __global__ void k_bglobalize(const int64_t* nnz_off, const int64_t* n_off, int32
 // ---------------------------------------------------------------------------
 #define PDHG_BDISPATCH_E(e, ...)   \
   switch (e) {                     \
+    case -4: {                     \
+      constexpr int E_ = -4;       \
+      __VA_ARGS__;                 \
+    } break;                       \
+    case -8: {                     \
+      constexpr int E_ = -8;       \
+      __VA_ARGS__;                 \
+    } break;                       \
     case 4: {                      \
       constexpr int E_ = 4;        \
       __VA_ARGS__;                 \
@@ -714,6 +722,8 @@ static cudaError_t configure_batch_kernels(size_t mx) {
   cudaError_t e = configure_batch_e<4>(mx);
   if (e == cudaSuccess) e = configure_batch_e<8>(mx);
   if (e == cudaSuccess) e = configure_batch_e<16>(mx);
+  if (e == cudaSuccess) e = configure_batch_e<-4>(mx);
+  if (e == cudaSuccess) e = configure_batch_e<-8>(mx);
   for (const void* f : {(const void*)k_bpow_Av<kBlock>, (const void*)k_bpow_ATu<kBlock>,
                         (const void*)k_brep_n<kBlock>, (const void*)k_brep_m<kBlock>,
                         (const void*)k_bws_z<kBlock>}) {
@@ -816,6 +826,115 @@ static pdhg_status batch_schedules(pdhg_ctx* ctx, int32_t** lp_a, int32_t** lp_t
   return PDHG_OK;
 }
 
+// Time the real batched primal (rows of A~^T) or dual (rows of A~) kernel.
+template <typename T>
+static pdhg_status time_batch_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out) {
+  const BatchBuffers<T> B = batch_buffers<T>(ctx);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int warm = 3, reps = 10;
+  ctx->launches += warm + reps;
+  for (int it = 0; it < warm + reps; ++it) {
+    if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
+    if (on_a) {
+      PDHG_BDISPATCH_E(B.it.a_sched.e,
+                       (k_bdual<T, kBlock, E_><<<ctx->l_dual.grid, kBlock, ctx->l_dual.smem,
+                                                  ctx->stream>>>(B, 0)));
+    } else {
+      PDHG_BDISPATCH_E(B.it.t_sched.e,
+                       (k_bprimal<T, kBlock, E_><<<ctx->l_prim.grid, kBlock, ctx->l_prim.smem,
+                                                    ctx->stream>>>(B, 0)));
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, ctx->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms / reps;
+  return PDHG_OK;
+}
+
+// LP-aligned iteration schedules picked by timing the candidates with the
+// real batched kernels on the initial state (zeroed again afterwards); E = 8
+// is kept unless another choice is more than 3% faster.
+static pdhg_status tune_batch_schedules(pdhg_ctx* ctx) {
+  const int count = ctx->count;
+  const bool mx = ctx->mixed;
+  for (int which = 0; which < 2; ++which) {
+    const bool on_a = which == 0;
+    const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
+    const int nrows = on_a ? ctx->m : ctx->n;
+    const int64_t* off = on_a ? ctx->h_m_off.data() : ctx->h_n_off.data();
+    int64_t longest = 0;
+    for (int r = 0; r < nrows; ++r) longest = std::max<int64_t>(longest, rp[r + 1] - rp[r]);
+    std::vector<int> cands = {kFixedE};
+    if (ctx->opt.autotune) {
+      cands = {4, 8, 16};
+      if (longest <= 256) cands.insert(cands.end(), {-4, -8});
+    }
+    DevSched best = on_a ? ctx->sa8 : ctx->st8;
+    int32_t* best_lp = on_a ? ctx->lp_a8_tiles : ctx->lp_t8_tiles;
+    float best_ms = 1e30f;
+    for (int e : cands) {
+      DevSched d;
+      int32_t* lpt = nullptr;
+      if (e == kFixedE) {
+        d = on_a ? ctx->sa8 : ctx->st8;
+        lpt = on_a ? ctx->lp_a8_tiles : ctx->lp_t8_tiles;
+      } else {
+        HostSched h = build_sched(rp.data(), nrows, e, off, count);
+        CKS(upload_sched(ctx, h, &d));
+        CKS(dalloc(ctx, &lpt, (size_t)count + 1));
+        CK(cudaMemcpyAsync(lpt, h.lp_tiles.data(), sizeof(int32_t) * (count + 1),
+                           cudaMemcpyHostToDevice, ctx->stream));
+      }
+      (on_a ? ctx->sa : ctx->st) = d;
+      if (on_a)
+        ctx->l_dual = make_launch(ctx, mx ? 2 : 3, d.view.e,
+                                  smem_for(0, mx, d.view.max_rows, d.view.e), d.view.ntiles);
+      else
+        ctx->l_prim = make_launch(ctx, mx ? 0 : 1, d.view.e,
+                                  smem_for(0, mx, d.view.max_rows, d.view.e), d.view.ntiles);
+      float ms = 0.f;
+      if (cands.size() > 1) {
+        if (mx)
+          CKS(time_batch_kernel<float>(ctx, on_a, &ms));
+        else
+          CKS(time_batch_kernel<double>(ctx, on_a, &ms));
+      }
+      const float bias = (e == 8) ? 0.97f : 1.0f;
+      if (ms * bias < best_ms) {
+        best_ms = ms * bias;
+        best = d;
+        best_lp = lpt;
+      }
+    }
+    (on_a ? ctx->sa : ctx->st) = best;
+    (on_a ? ctx->lp_a_tiles : ctx->lp_t_tiles) = best_lp;
+  }
+  const SchedView &A = ctx->sa.view, &T = ctx->st.view;
+  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, T.e, smem_for(0, mx, T.max_rows, T.e), T.ntiles);
+  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, A.e, smem_for(0, mx, A.max_rows, A.e), A.ntiles);
+  ctx->l_eval = make_launch(ctx, mx ? 4 : 5, T.e, smem_for(1, mx, T.max_rows, T.e),
+                            std::max(T.ntiles, A.ntiles));
+  if (std::max(A.ntiles, T.ntiles) > ctx->rec_tiles) {
+    ctx->rec_tiles = std::max(A.ntiles, T.ntiles);
+    CKS(dalloc(ctx, &ctx->rec_t, (size_t)ctx->rec_tiles * kEvalQ));
+    CKS(dalloc(ctx, &ctx->rec_a, (size_t)ctx->rec_tiles * kEvalQ));
+  }
+  const size_t es = elem(ctx);
+  for (void* p : {ctx->x, ctx->x_avg, ctx->x_last})
+    CK(cudaMemsetAsync(p, 0, es * ctx->n, ctx->stream));
+  for (void* p : {ctx->y, ctx->y_avg, ctx->y_last, ctx->Ax, ctx->Ax_avg})
+    CK(cudaMemsetAsync(p, 0, es * ctx->m, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
 static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int32_t* n,
                                      const int32_t* row_ptr, const int32_t* col,
                                      const double* val, const double* b, const double* c) {
@@ -894,23 +1013,27 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
   }
   CKS(prepare_matrix(ctx));
 
-  // LP-aligned schedules: iteration (E = 8) and float64 (kFixedE)
-  CKS(batch_schedules(ctx, &ctx->lp_a_tiles, &ctx->lp_t_tiles, &ctx->sa, &ctx->st, 8));
-  ctx->sa8 = ctx->sa;
-  ctx->st8 = ctx->st;
-  ctx->lp_a8_tiles = ctx->lp_a_tiles;
-  ctx->lp_t8_tiles = ctx->lp_t_tiles;
+  // LP-aligned float64 schedules (set-up, report, adjoint); the iteration
+  // schedules start as the same and are tuned once the scalars exist
+  CKS(batch_schedules(ctx, &ctx->lp_a8_tiles, &ctx->lp_t8_tiles, &ctx->sa8, &ctx->st8, kFixedE));
+  ctx->sa = ctx->sa8;
+  ctx->st = ctx->st8;
+  ctx->lp_a_tiles = ctx->lp_a8_tiles;
+  ctx->lp_t_tiles = ctx->lp_t8_tiles;
   const bool mx = ctx->mixed;
   const SchedView &A = ctx->sa.view, &T = ctx->st.view;
-  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, T.e, smem_for(0, mx, T.max_rows), T.ntiles);
-  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, A.e, smem_for(0, mx, A.max_rows), A.ntiles);
-  ctx->l_eval = make_launch(ctx, mx ? 4 : 5, T.e, smem_for(1, mx, T.max_rows),
+  const SchedView &A8 = ctx->sa8.view, &T8 = ctx->st8.view;
+  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, T.e, smem_for(0, mx, T.max_rows, T.e), T.ntiles);
+  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, A.e, smem_for(0, mx, A.max_rows, A.e), A.ntiles);
+  ctx->l_eval = make_launch(ctx, mx ? 4 : 5, T.e, smem_for(1, mx, T.max_rows, T.e),
                             std::max(T.ntiles, A.ntiles));
-  ctx->l_a64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, A.max_rows), A.ntiles);
-  ctx->l_t64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, T.max_rows), T.ntiles);
+  ctx->l_a64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, A8.max_rows, A8.e), A8.ntiles);
+  ctx->l_t64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, T8.max_rows, T8.e), T8.ntiles);
   ctx->restart_grid = std::max(1, std::min(ctx->nsm * 8, std::max(A.ntiles, T.ntiles)));
-  CKS(dalloc(ctx, &ctx->rec_t, (size_t)std::max(T.ntiles, 1) * kEvalQ));
-  CKS(dalloc(ctx, &ctx->rec_a, (size_t)std::max(A.ntiles, 1) * kEvalQ));
+  // per-tile records; tune_batch_schedules grows them for the tuned schedules
+  ctx->rec_tiles = std::max({A.ntiles, T.ntiles, A8.ntiles, T8.ntiles, 1});
+  CKS(dalloc(ctx, &ctx->rec_t, (size_t)ctx->rec_tiles * kEvalQ));
+  CKS(dalloc(ctx, &ctx->rec_a, (size_t)ctx->rec_tiles * kEvalQ));
   CKS(dalloc(ctx, &ctx->active, 4));
   CKS(dalloc(ctx, &ctx->breport, (size_t)count * 8));
   CK(cudaMemsetAsync(ctx->active, 0, 4 * sizeof(int32_t), ctx->stream));
@@ -937,16 +1060,16 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
     k_bpow_init<<<(count + 255) / 256, 256, 0, ctx->stream>>>(ctx->ps, count,
                                                                ctx->opt.power_max_iter,
                                                                ctx->opt.power_rel_tol);
-    k_bpow_norm<<<ctx->restart_grid, 256, 0, ctx->stream>>>(T, w, v, ctx->ps, d_n_off, 1);
+    k_bpow_norm<<<ctx->restart_grid, 256, 0, ctx->stream>>>(T8, w, v, ctx->ps, d_n_off, 1);
     ctx->launches += 2;
     std::vector<PowerState> hp(count);
     for (int it = 0; it < ctx->opt.power_max_iter; ++it) {
       k_bpow_Av<kBlock><<<ctx->l_a64.grid, kBlock, ctx->l_a64.smem, ctx->stream>>>(
-          A, ctx->a_rp, ctx->a_col, ctx->a_val64, v, u, ctx->ps);
+          A8, ctx->a_rp, ctx->a_col, ctx->a_val64, v, u, ctx->ps);
       k_bpow_ATu<kBlock><<<ctx->l_t64.grid, kBlock, ctx->l_t64.smem, ctx->stream>>>(
-          T, ctx->t_rp, ctx->t_col, ctx->t_val64, u, v, w, ctx->rec_t, ctx->ps, ctx->lp_t_tiles,
+          T8, ctx->t_rp, ctx->t_col, ctx->t_val64, u, v, w, ctx->rec_t, ctx->ps, ctx->lp_t8_tiles,
           count, ticket);
-      k_bpow_norm<<<ctx->restart_grid, 256, 0, ctx->stream>>>(T, w, v, ctx->ps, d_n_off, 0);
+      k_bpow_norm<<<ctx->restart_grid, 256, 0, ctx->stream>>>(T8, w, v, ctx->ps, d_n_off, 0);
       ctx->launches += 3;
       if ((it & 15) == 15) {
         CK(cudaMemcpyAsync(hp.data(), ctx->ps, sizeof(PowerState) * count, cudaMemcpyDeviceToHost,
@@ -965,6 +1088,7 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
   ctx->launches += 1;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
+  CKS(tune_batch_schedules(ctx));
   CKS(polling_resources(ctx));
   return PDHG_OK;
 }
@@ -1144,13 +1268,13 @@ extern "C" pdhg_status pdhg_batch_get(pdhg_ctx* ctx, double* x, double* y, doubl
   const int count = ctx->count;
   CKS(batch_returned64(ctx));
   k_brep_n<kBlock><<<ctx->l_t64.grid, kBlock, ctx->l_t64.smem, ctx->stream>>>(
-      ctx->st.view, ctx->t_rp, ctx->t_col, ctx->t_val64, ctx->xs64, ctx->ys64, ctx->c_t64,
+      ctx->st8.view, ctx->t_rp, ctx->t_col, ctx->t_val64, ctx->xs64, ctx->ys64, ctx->c_t64,
       ctx->D_c, ctx->out_n1, ctx->out_n2, ctx->rec_t);
   k_brep_m<kBlock><<<ctx->l_a64.grid, kBlock, ctx->l_a64.smem, ctx->stream>>>(
-      ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64, ctx->xs64, ctx->ys64, ctx->b_t64,
+      ctx->sa8.view, ctx->a_rp, ctx->a_col, ctx->a_val64, ctx->xs64, ctx->ys64, ctx->b_t64,
       ctx->D_r, ctx->out_m1, ctx->rec_a);
-  k_brep_final<<<(count + 255) / 256, 256, 0, ctx->stream>>>(ctx->rec_t, ctx->lp_t_tiles,
-                                                             ctx->rec_a, ctx->lp_a_tiles, count,
+  k_brep_final<<<(count + 255) / 256, 256, 0, ctx->stream>>>(ctx->rec_t, ctx->lp_t8_tiles,
+                                                             ctx->rec_a, ctx->lp_a8_tiles, count,
                                                              ctx->breport);
   ctx->launches += 3;
   CK(cudaGetLastError());
@@ -1197,12 +1321,12 @@ extern "C" pdhg_status pdhg_batch_warmstart_point(pdhg_ctx* ctx, double mu_min, 
                      cudaMemcpyHostToDevice, ctx->stream));
   double* zs = ctx->out_n2;
   k_bws_z<kBlock><<<ctx->l_t64.grid, kBlock, ctx->l_t64.smem, ctx->stream>>>(
-      ctx->st.view, ctx->t_rp, ctx->t_col, ctx->t_val64, ctx->xs64, ctx->ys64, ctx->c_t64, zs,
+      ctx->st8.view, ctx->t_rp, ctx->t_col, ctx->t_val64, ctx->xs64, ctx->ys64, ctx->c_t64, zs,
       ctx->rec_t);
-  k_bws_mu<<<(count + 255) / 256, 256, 0, ctx->stream>>>(ctx->rec_t, ctx->lp_t_tiles, d_n_off,
+  k_bws_mu<<<(count + 255) / 256, 256, 0, ctx->stream>>>(ctx->rec_t, ctx->lp_t8_tiles, d_n_off,
                                                          count, mu_min, mu);
   k_bws_apply<<<ctx->restart_grid, 256, 0, ctx->stream>>>(
-      ctx->st.view, ctx->sa.view, ctx->xs64, zs, ctx->ys64, mu, delta_max, alpha_min, unscaled,
+      ctx->st8.view, ctx->sa8.view, ctx->xs64, zs, ctx->ys64, mu, delta_max, alpha_min, unscaled,
       ctx->D_r, ctx->D_c, ctx->out_n1, ctx->out_m1, zs);
   ctx->launches += 3;
   CK(cudaGetLastError());

@@ -106,6 +106,7 @@ struct pdhg_ctx {
   int32_t *lp_a_tiles = nullptr, *lp_t_tiles = nullptr;    // [count + 1] tile ranges
   int32_t *lp_a8_tiles = nullptr, *lp_t8_tiles = nullptr;  // same, float64 schedules
   double *rec_t = nullptr, *rec_a = nullptr;  // per-tile evaluation / report records
+  int rec_tiles = 0;                          // tiles the record arrays hold
   int32_t* active = nullptr;                  // LPs not finished after the last evaluation
   double* breport = nullptr;                  // [count][8] per-LP report
   void* adjoint = nullptr;                    // active-set polish / adjoint buffers
@@ -149,10 +150,12 @@ pdhg_status dalloc(pdhg_ctx* ctx, T** p, size_t count) {
 pdhg_status copy_in(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes);
 pdhg_status copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes);
 // kind 0: one gathered vector in the iteration precision, 1: two, 2: one in float64
-size_t smem_for(int kind, bool mixed, int max_rows);
+size_t smem_for(int kind, bool mixed, int max_rows, int e);
 pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d);
 Launch make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int ntiles);
 size_t elem(const pdhg_ctx* ctx);
+// mean duration of a plain SpMV over schedule d (A when on_a, else A^T)
+pdhg_status time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float* ms_out);
 // create stages shared by the single-LP and batched paths
 pdhg_status setup_device(pdhg_ctx* ctx);
 pdhg_status alloc_arrays(pdhg_ctx* ctx);

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(BLOCK) k_primal(IterBuffers<T> B, int i) {
   const long long tt = B.sc->t + i;  // iterations since restart before this one
   PrimalEpi<T> epi{B.x, B.c_t, B.x_avg, (T)B.sc->tau, (T)(1.0 / (double)(tt + 1)), tt == 0};
   Gather<T, 1> g{{B.y}};
-  run_tiles<T, 1, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
+  run_sched<T, 1, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(BLOCK) k_dual(IterBuffers<T> B, int i) {
   DualEpi<T> epi{B.y,   B.b_t, B.Ax, B.y_avg, B.Ax_avg, (T)B.sc->sigma, (T)(1.0 / (double)(tt + 1)),
                  tt == 0};
   Gather<T, 1> g{{B.x}};
-  run_tiles<T, 1, BLOCK, E>(B.a_sched, B.a_rp, B.a_col, B.a_val, g, epi, smem);
+  run_sched<T, 1, BLOCK, E>(B.a_sched, B.a_rp, B.a_col, B.a_val, g, epi, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
 #pragma unroll
     for (int k = 0; k < Q_N; ++k) epi.q[c][k] = 0.0;
   Gather<T, 2> g{{B.y, B.y_avg}};
-  run_tiles<T, 2, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
+  run_sched<T, 2, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
   // m side: primal residual, dual objective, distance to the last restart point
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < B.m; i += gridDim.x * BLOCK) {
     const double bi = B.b_t64[i], dr = B.D_r[i], yl = (double)B.y_last[i];
@@ -214,6 +214,14 @@ __global__ void k_restart(IterBuffers<T> B) {
 // nonzeros per thread of a schedule -> template instantiation
 #define PDHG_DISPATCH_E(e, ...)                 \
   switch (e) {                                  \
+    case -4: {                                  \
+      constexpr int E_ = -4;                    \
+      __VA_ARGS__;                              \
+    } break;                                    \
+    case -8: {                                  \
+      constexpr int E_ = -8;                    \
+      __VA_ARGS__;                              \
+    } break;                                    \
     case 4: {                                   \
       constexpr int E_ = 4;                     \
       __VA_ARGS__;                              \
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(BLOCK) k_spmv(SchedView S, const int32_t* rp, 
   extern __shared__ __align__(16) unsigned char smem[];
   StoreEpi<T> epi{out};
   Gather<T, 1> g{{v}};
-  run_tiles<T, 1, BLOCK, E>(S, rp, col, val, g, epi, smem);
+  run_sched<T, 1, BLOCK, E>(S, rp, col, val, g, epi, smem);
 }
 
 template <typename T>
@@ -547,8 +555,16 @@ PDHG_INST(float)
 PDHG_INST(double)
 #undef PDHG_INST
 
-// shared memory of the tile kernels (NV vectors, precision, rows per tile)
-size_t tile_smem(int nv, bool f32, int max_rows) {
+// shared memory of the tile kernels (NV vectors, precision, rows per tile,
+// schedule variant: e < 0 is the vector kernel)
+size_t tile_smem(int nv, bool f32, int max_rows, int e) {
+  if (e < 0) {
+    if (nv == 1)
+      return f32 ? tile_vec_smem_bytes<float, 1, kBlock>(max_rows)
+                 : tile_vec_smem_bytes<double, 1, kBlock>(max_rows);
+    return f32 ? tile_vec_smem_bytes<float, 2, kBlock>(max_rows)
+               : tile_vec_smem_bytes<double, 2, kBlock>(max_rows);
+  }
   if (nv == 1) return f32 ? tile_smem_bytes<float, 1, kBlock>(max_rows)
                           : tile_smem_bytes<double, 1, kBlock>(max_rows);
   return f32 ? tile_smem_bytes<float, 2, kBlock>(max_rows) : tile_smem_bytes<double, 2, kBlock>(max_rows);
@@ -590,7 +606,8 @@ static const void* fixed_kernel(int which) {
 cudaError_t configure_tile_kernels(size_t max_smem) {
   cudaError_t e = cudaSuccess;
   for (int w = 0; w < 8; ++w)
-    for (const void* f : {tile_kernel<4>(w), tile_kernel<8>(w), tile_kernel<16>(w)}) {
+    for (const void* f : {tile_kernel<4>(w), tile_kernel<8>(w), tile_kernel<16>(w),
+                          tile_kernel<-4>(w), tile_kernel<-8>(w)}) {
       cudaError_t r = set_max_dyn(f, max_smem);
       if (r != cudaSuccess) e = r;
     }
@@ -609,6 +626,10 @@ int tile_occupancy(int which, int e, size_t smem) {
     f = fixed_kernel(0);
   else if (e == 4)
     f = tile_kernel<4>(which);
+  else if (e == -4)
+    f = tile_kernel<-4>(which);
+  else if (e == -8)
+    f = tile_kernel<-8>(which);
   else if (e == 16)
     f = tile_kernel<16>(which);
   else

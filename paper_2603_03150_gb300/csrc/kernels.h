@@ -129,6 +129,6 @@ void launch_init_scalars(Scalars* sc, const double* sums, const PowerState* ps,
 cudaError_t configure_setup_kernels(size_t max_smem);
 cudaError_t configure_tile_kernels(size_t max_smem);
 int tile_occupancy(int which, int e, size_t smem);
-size_t tile_smem(int nv, bool f32, int max_rows);
+size_t tile_smem(int nv, bool f32, int max_rows, int e);
 
 }  // namespace pdhg

@@ -52,7 +52,8 @@ namespace pdhg {
 // of capacity-sized chunks.
 HostSched build_sched(const int32_t* rp, int nrows, int e, const int64_t* lp_off, int count) {
   HostSched h;
-  const int cap = tile_capacity(kBlock, e);
+  // vector schedules (e < 0) use the tile capacity of e = 8
+  const int cap = tile_capacity(kBlock, e > 0 ? e : 8);
   h.tile_nnz = cap;
   h.max_rows = tile_max_rows(kBlock);
   h.e = e;
@@ -117,10 +118,10 @@ pdhg_status pdhg::copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t byt
 }
 
 // kind 0: one gathered vector in the iteration precision, 1: two, 2: one in float64
-size_t pdhg::smem_for(int kind, bool mixed, int max_rows) {
-  if (kind == 0) return tile_smem(1, mixed, max_rows);
-  if (kind == 1) return tile_smem(2, mixed, max_rows);
-  return tile_smem(1, false, max_rows);
+size_t pdhg::smem_for(int kind, bool mixed, int max_rows, int e) {
+  if (kind == 0) return tile_smem(1, mixed, max_rows, e);
+  if (kind == 1) return tile_smem(2, mixed, max_rows, e);
+  return tile_smem(1, false, max_rows, e);
 }
 
 pdhg_status pdhg::upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) {
@@ -158,8 +159,8 @@ Launch pdhg::make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int nt
 }
 
 // Time one SpMV schedule candidate (mean of a few launches after warm-up).
-static pdhg_status time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float* ms_out) {
-  const size_t smem = smem_for(0, ctx->mixed, d.view.max_rows);
+pdhg_status pdhg::time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float* ms_out) {
+  const size_t smem = smem_for(0, ctx->mixed, d.view.max_rows, d.view.e);
   Launch L = make_launch(ctx, ctx->mixed ? 6 : 7, d.view.e, smem, d.view.ntiles);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -195,66 +196,28 @@ static pdhg_status time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float*
   return PDHG_OK;
 }
 
-static pdhg_status choose_schedules(pdhg_ctx* ctx) {
-  std::vector<int> cands;
-  if (ctx->opt.tile_nnz > 0)
-    cands.push_back(ctx->opt.tile_nnz <= 1024 ? 4 : (ctx->opt.tile_nnz <= 2048 ? 8 : 16));
-  else if (ctx->opt.autotune)
-    cands = {4, 8, 16};
-  else
-    cands = {8};
+// Float64 schedules (report, Algorithm 1, power iteration) and reduction
+// scratch sized for any iteration schedule the tuner may pick.
+static pdhg_status fixed_schedules(pdhg_ctx* ctx) {
+  int64_t long_rows = 0;  // rows that any candidate schedule could split
   for (int which = 0; which < 2; ++which) {
     const bool on_a = which == 0;
     const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
     const int nrows = on_a ? ctx->m : ctx->n;
-    DevSched best{};
-    float best_ms = 1e30f;
-    for (int e : cands) {
-      HostSched h = build_sched(rp.data(), nrows, e);
-      DevSched d;
-      CKS(upload_sched(ctx, h, &d));
-      float ms = 0.f;
-      if (cands.size() > 1) CKS(time_spmv(ctx, d, on_a, &ms));
-      // E = 8 is kept unless another choice is more than 3% faster, so timing
-      // noise does not flip the schedule from one context to the next
-      const float bias = (e == 8) ? 0.97f : 1.0f;
-      if (ms * bias < best_ms) {
-        best_ms = ms * bias;
-        best = d;
-      }
-    }
-    (on_a ? ctx->sa : ctx->st) = best;
-    // the float64 kernels (report, Algorithm 1, power iteration) use kFixedE
-    if (best.view.e == kFixedE) {
-      (on_a ? ctx->sa8 : ctx->st8) = best;
-    } else {
-      HostSched h = build_sched(rp.data(), nrows, kFixedE);
-      CKS(upload_sched(ctx, h, on_a ? &ctx->sa8 : &ctx->st8));
-    }
+    HostSched h = build_sched(rp.data(), nrows, kFixedE);
+    CKS(upload_sched(ctx, h, on_a ? &ctx->sa8 : &ctx->st8));
+    for (int r = 0; r < nrows; ++r) long_rows += (rp[r + 1] - rp[r]) > tile_capacity(kBlock, 4);
   }
-  // launch shapes
   const bool mx = ctx->mixed;
-  const SchedView &A = ctx->sa.view, &T = ctx->st.view;
   const SchedView &A8 = ctx->sa8.view, &T8 = ctx->st8.view;
-  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, T.e, smem_for(0, mx, T.max_rows), T.ntiles);
-  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, A.e, smem_for(0, mx, A.max_rows), A.ntiles);
-  {
-    const size_t sm = smem_for(1, mx, T.max_rows);
-    const int occ = tile_occupancy(mx ? 4 : 5, T.e, sm);
-    // the eval kernel also walks the m rows elementwise: at least enough blocks for that
-    int grid = std::max(T.ntiles, (ctx->m + kBlock - 1) / kBlock);
-    grid = std::max(1, std::min(grid, ctx->nsm * occ));
-    ctx->l_eval = Launch{grid, sm};
-  }
-  ctx->l_a64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, A8.max_rows), A8.ntiles);
-  ctx->l_t64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, T8.max_rows), T8.ntiles);
+  ctx->l_a64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, A8.max_rows, A8.e), A8.ntiles);
+  ctx->l_t64 = make_launch(ctx, 8, kFixedE, smem_for(2, mx, T8.max_rows, T8.e), T8.ntiles);
   ctx->restart_grid = std::max(1, std::min(ctx->nsm * 8, (std::max(ctx->m, ctx->n) + 255) / 256));
-  // reduction scratch: the largest grid plus split records, kEvalQ doubles each
-  const int gmax = std::max({ctx->l_eval.grid, ctx->l_a64.grid, ctx->l_t64.grid, 4096});
-  const int groups = std::max({A.ngroups, T.ngroups, A8.ngroups, T8.ngroups});
-  ctx->partials_len = (size_t)(gmax + groups + 1) * kEvalQ;
+  // grids never exceed SMs x 8 resident blocks of 256 threads
+  const int64_t gmax = std::max<int64_t>({(int64_t)ctx->nsm * 8, ctx->l_a64.grid, ctx->l_t64.grid, 4096});
+  ctx->partials_len = (size_t)(gmax + long_rows + 1) * kEvalQ;
   CKS(dalloc(ctx, &ctx->partials, ctx->partials_len));
-  CKS(dalloc(ctx, &ctx->split_q, (size_t)(T.ngroups + 1) * kEvalQ));
+  CKS(dalloc(ctx, &ctx->split_q, (size_t)(long_rows + 1) * kEvalQ));
   return PDHG_OK;
 }
 
@@ -328,6 +291,110 @@ static void enqueue_chunk_any(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
     enqueue_chunk<float>(ctx, len, timing);
   else
     enqueue_chunk<double>(ctx, len, timing);
+}
+
+// Iteration schedules: every candidate is timed with the real fused primal
+// (rows of A~^T) or dual (rows of A~) kernel on the initial state; the state
+// is zeroed again afterwards.  e > 0: segmented kernel with e nonzeros per
+// thread; e < 0: vector kernel with -e lanes per row (only if all rows are
+// short).  E = 8 is kept unless another choice is more than 3% faster, so
+// timing noise does not flip the schedule from one context to the next.
+template <typename T>
+static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out) {
+  const IterBuffers<T> B = iter_buffers<T>(ctx);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int warm = 3, reps = 10;
+  ctx->launches += warm + reps;
+  for (int it = 0; it < warm + reps; ++it) {
+    if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
+    if (on_a)
+      launch_dual<T>(B, ctx->l_dual, 0, ctx->stream);
+    else
+      launch_primal<T>(B, ctx->l_prim, 0, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, ctx->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms / reps;
+  return PDHG_OK;
+}
+
+static pdhg_status tune_schedules(pdhg_ctx* ctx) {
+  const bool mx = ctx->mixed;
+  for (int which = 0; which < 2; ++which) {
+    const bool on_a = which == 0;
+    const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
+    const int nrows = on_a ? ctx->m : ctx->n;
+    int64_t longest = 0;
+    for (int r = 0; r < nrows; ++r) longest = std::max<int64_t>(longest, rp[r + 1] - rp[r]);
+    std::vector<int> cands;
+    if (ctx->opt.tile_nnz < 0)  // forced vector variant (only where rows are short)
+      cands.push_back(longest <= 256 ? (ctx->opt.tile_nnz <= -8 ? -8 : -4) : 8);
+    else if (ctx->opt.tile_nnz > 0)
+      cands.push_back(ctx->opt.tile_nnz <= 1024 ? 4 : (ctx->opt.tile_nnz <= 2048 ? 8 : 16));
+    else if (ctx->opt.autotune) {
+      cands = {4, 8, 16};
+      if (longest <= 256) cands.insert(cands.end(), {-4, -8});
+    } else {
+      cands = {8};
+    }
+    DevSched best{};
+    float best_ms = 1e30f;
+    for (int e : cands) {
+      DevSched d;
+      if (e == kFixedE) {
+        d = on_a ? ctx->sa8 : ctx->st8;
+      } else {
+        HostSched h = build_sched(rp.data(), nrows, e);
+        CKS(upload_sched(ctx, h, &d));
+      }
+      (on_a ? ctx->sa : ctx->st) = d;
+      if (on_a)
+        ctx->l_dual = make_launch(ctx, mx ? 2 : 3, d.view.e,
+                                  smem_for(0, mx, d.view.max_rows, d.view.e), d.view.ntiles);
+      else
+        ctx->l_prim = make_launch(ctx, mx ? 0 : 1, d.view.e,
+                                  smem_for(0, mx, d.view.max_rows, d.view.e), d.view.ntiles);
+      float ms = 0.f;
+      if (cands.size() > 1) {
+        if (mx)
+          CKS(time_iteration_kernel<float>(ctx, on_a, &ms));
+        else
+          CKS(time_iteration_kernel<double>(ctx, on_a, &ms));
+      }
+      const float bias = (e == 8) ? 0.97f : 1.0f;
+      if (ms * bias < best_ms) {
+        best_ms = ms * bias;
+        best = d;
+      }
+    }
+    (on_a ? ctx->sa : ctx->st) = best;
+  }
+  const SchedView &A = ctx->sa.view, &T = ctx->st.view;
+  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, T.e, smem_for(0, mx, T.max_rows, T.e), T.ntiles);
+  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, A.e, smem_for(0, mx, A.max_rows, A.e), A.ntiles);
+  {
+    const size_t sm = smem_for(1, mx, T.max_rows, T.e);
+    const int occ = tile_occupancy(mx ? 4 : 5, T.e, sm);
+    // the eval kernel also walks the m rows elementwise: at least enough blocks for that
+    int grid = std::max(T.ntiles, (ctx->m + kBlock - 1) / kBlock);
+    grid = std::max(1, std::min(grid, ctx->nsm * occ));
+    ctx->l_eval = Launch{grid, sm};
+  }
+  // the tuning launches moved the iterate: back to x = 0, y = 0
+  const size_t es = elem(ctx);
+  for (void* p : {ctx->x, ctx->x_avg, ctx->x_last})
+    CK(cudaMemsetAsync(p, 0, es * ctx->n, ctx->stream));
+  for (void* p : {ctx->y, ctx->y_avg, ctx->y_last, ctx->Ax, ctx->Ax_avg})
+    CK(cudaMemsetAsync(p, 0, es * ctx->m, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
 }
 
 static pdhg_status build_graphs(pdhg_ctx* ctx) {
@@ -586,8 +653,8 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
   CKS(upload_lp(ctx, col, val, b, c));
   CKS(prepare_matrix(ctx));
 
-  // tile schedules
-  CKS(choose_schedules(ctx));
+  // float64 schedules (the iteration schedules are tuned once the scalars exist)
+  CKS(fixed_schedules(ctx));
 
   // a3: power iteration on A~^T A~ (float64)
   {
@@ -641,6 +708,7 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     ctx->power_iters = hp.k;
   }
 
+  CKS(tune_schedules(ctx));
   CKS(polling_resources(ctx));
   return PDHG_OK;
 }
@@ -680,9 +748,9 @@ extern "C" pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const i
     pdhg_default_options(&ctx->opt);
   if (ctx->opt.eval_freq < 1 || ctx->opt.ruiz_iters < 0 || ctx->opt.power_max_iter < 0 ||
       (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED) ||
-      ctx->opt.tile_nnz < 0 || ctx->opt.tile_nnz > 8192) {
+      ctx->opt.tile_nnz < -8 || ctx->opt.tile_nnz > 8192) {
     set_error("invalid options (eval_freq >= 1, ruiz_iters >= 0, precision 0/1, "
-              "0 <= tile_nnz <= 8192)");
+              "-8 <= tile_nnz <= 8192)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }

@@ -277,4 +277,128 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Vector variant for matrices whose rows are all short: G consecutive lanes
+// own one row, read its nonzeros with a G-strided loop straight from global
+// memory, gather, and reduce with shuffles; the row sums are staged in shared
+// memory and the epilogue runs as one coalesced loop over the tile's rows
+// (two block barriers per tile, no row search or carry scan).  Split tiles
+// reduce over the whole block as above.
+// ---------------------------------------------------------------------------
+template <typename T, int NV, int BLOCK, int G, class Epi>
+__device__ __forceinline__ void run_tiles_vec(const SchedView& S, const int32_t* __restrict__ row_ptr,
+                                              const int32_t* __restrict__ col,
+                                              const T* __restrict__ val, const Gather<T, NV>& g,
+                                              Epi& epi, unsigned char* smem) {
+  static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "G must be a power of two <= 32");
+  constexpr int NW = BLOCK / 32;
+  const int rstride = S.max_rows + 4;
+  T* rsum = reinterpret_cast<T*>(smem);
+  T* wsum = rsum + NV * rstride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = tid / G, gl = tid & (G - 1);
+  constexpr int NG = BLOCK / G;
+  for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+    const Tile tl = S.tiles[t];
+    if (!epi_begin(epi, tl, 0)) continue;
+    if (tl.split >= 0) {
+      T s[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s[v] = T(0);
+      for (int k = tl.nz_begin + tid; k < tl.nz_end; k += BLOCK) {
+        const T a = __ldg(val + k);
+        const int c = __ldg(col + k);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s[v] += a * __ldg(g.v[v] + c);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        s[v] = warp_sum(s[v]);
+        if (lane == 0) wsum[v * NW + warp] = s[v];
+      }
+      __syncthreads();
+      if (tid == 0) {
+        T part[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          part[v] = T(0);
+          for (int w = 0; w < NW; ++w) part[v] += wsum[v * NW + w];
+        }
+        T* slots = reinterpret_cast<T*>(S.slots);
+        const SplitGroup sg = S.groups[tl.split];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) slots[(size_t)(sg.slot0 + tl.part) * NV + v] = part[v];
+        __threadfence();
+        const int prev = atomicAdd(S.counters + tl.split, 1);
+        if (prev == sg.nparts - 1) {
+          __threadfence();
+          T tot[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) tot[v] = T(0);
+          for (int pp = 0; pp < sg.nparts; ++pp)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tot[v] += __ldcg(slots + (size_t)(sg.slot0 + pp) * NV + v);
+          S.counters[tl.split] = 0;
+          epi.row(sg.row, tot, tl.split);
+        }
+      }
+      __syncthreads();
+      epi_end(epi, tl, t, 0);
+      continue;
+    }
+    const int nrows = tl.row_end - tl.row_begin;
+    // every lane walks the same number of group rounds (shuffles need all 32)
+    for (int r0 = 0; r0 < nrows; r0 += NG) {
+      const int r = tl.row_begin + r0 + grp;
+      T s[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s[v] = T(0);
+      if (r0 + grp < nrows) {
+        const int e = __ldg(row_ptr + r + 1);
+        for (int k = __ldg(row_ptr + r) + gl; k < e; k += G) {
+          const T a = __ldg(val + k);
+          const int c = __ldg(col + k);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) s[v] += a * __ldg(g.v[v] + c);
+        }
+      }
+#pragma unroll
+      for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s[v] += __shfl_down_sync(0xffffffffu, s[v], o, G);
+      if (gl == 0 && r0 + grp < nrows)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) rsum[v * rstride + r0 + grp] = s[v];
+    }
+    __syncthreads();
+    for (int r = tid; r < nrows; r += BLOCK) {
+      T s[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s[v] = rsum[v * rstride + r];
+      epi.row(tl.row_begin + r, s, -1);
+    }
+    __syncthreads();
+    epi_end(epi, tl, t, 0);
+  }
+}
+
+// Schedule variant V: V > 0 segmented with E = V nonzeros per thread,
+// V < 0 vector with G = -V lanes per row.
+template <typename T, int NV, int BLOCK, int V, class Epi>
+__device__ __forceinline__ void run_sched(const SchedView& S, const int32_t* __restrict__ row_ptr,
+                                          const int32_t* __restrict__ col,
+                                          const T* __restrict__ val, const Gather<T, NV>& g,
+                                          Epi& epi, unsigned char* smem) {
+  if constexpr (V > 0)
+    run_tiles<T, NV, BLOCK, V>(S, row_ptr, col, val, g, epi, smem);
+  else
+    run_tiles_vec<T, NV, BLOCK, -V>(S, row_ptr, col, val, g, epi, smem);
+}
+
+// Shared memory of run_tiles_vec (staged row sums, split-tile block sums).
+template <typename T, int NV, int BLOCK>
+__host__ __device__ constexpr size_t tile_vec_smem_bytes(int max_rows) {
+  return sizeof(T) * (size_t)NV * (max_rows + 4) + sizeof(T) * (size_t)NV * (BLOCK / 32) + 16;
+}
+
 }  // namespace pdhg
