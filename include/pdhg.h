@@ -72,10 +72,12 @@ typedef struct pdhg_options {
   int32_t use_graphs;      /* 1 (default): replay each F-iteration chunk as a
                               CUDA graph                                        */
   int32_t autotune;        /* 1 (default): time SpMV tile schedules at create   */
-  int32_t tile_nnz;        /* 0: autotune; > 0: segmented SpMV tiles of about
-                              this many nonzeros; -4 / -8: the vector SpMV with
-                              4 / 8 lanes per row (matrices whose rows all have
-                              <= 256 nonzeros; others fall back to segmented)  */
+  int32_t tile_nnz;        /* 0: autotune; > 0: segmented SpMV tiles of up to
+                              2044 (tile_nnz <= 2048), 4092 (<= 4096) or 8188
+                              nonzeros (8 / 16 / 32 per thread); -4 / -8: the
+                              vector SpMV with 4 / 8 lanes per row (matrices
+                              whose rows all have <= 256 nonzeros; others fall
+                              back to segmented)                               */
   int32_t kernel_timing;   /* 1: sample primal/dual kernel durations with CUDA
                               events during pdhg_solve                          */
   int32_t verbose;

@@ -682,8 +682,8 @@ __global__ void k_bglobalize(const int64_t* nnz_off, const int64_t* n_off, int32
       constexpr int E_ = -8;       \
       __VA_ARGS__;                 \
     } break;                       \
-    case 4: {                      \
-      constexpr int E_ = 4;        \
+    case 32: {                     \
+      constexpr int E_ = 32;       \
       __VA_ARGS__;                 \
     } break;                       \
     case 16: {                     \
@@ -719,8 +719,8 @@ static cudaError_t configure_batch_e(size_t mx) {
 }
 
 static cudaError_t configure_batch_kernels(size_t mx) {
-  cudaError_t e = configure_batch_e<4>(mx);
-  if (e == cudaSuccess) e = configure_batch_e<8>(mx);
+  cudaError_t e = configure_batch_e<8>(mx);
+  if (e == cudaSuccess) e = configure_batch_e<32>(mx);
   if (e == cudaSuccess) e = configure_batch_e<16>(mx);
   if (e == cudaSuccess) e = configure_batch_e<-4>(mx);
   if (e == cudaSuccess) e = configure_batch_e<-8>(mx);
@@ -814,8 +814,8 @@ static pdhg_status batch_schedules(pdhg_ctx* ctx, int32_t** lp_a, int32_t** lp_t
                                    DevSched* st, int e) {
   HostSched ha = build_sched(ctx->h_a_rp.data(), ctx->m, e, ctx->h_m_off.data(), ctx->count);
   HostSched ht = build_sched(ctx->h_t_rp.data(), ctx->n, e, ctx->h_n_off.data(), ctx->count);
-  CKS(upload_sched(ctx, ha, sa));
-  CKS(upload_sched(ctx, ht, st));
+  CKS(upload_sched(ctx, ha, sa, ctx->a_rp));
+  CKS(upload_sched(ctx, ht, st, ctx->t_rp));
   CKS(dalloc(ctx, lp_a, (size_t)ctx->count + 1));
   CKS(dalloc(ctx, lp_t, (size_t)ctx->count + 1));
   CK(cudaMemcpyAsync(*lp_a, ha.lp_tiles.data(), sizeof(int32_t) * (ctx->count + 1),
@@ -873,7 +873,7 @@ static pdhg_status tune_batch_schedules(pdhg_ctx* ctx) {
     for (int r = 0; r < nrows; ++r) longest = std::max<int64_t>(longest, rp[r + 1] - rp[r]);
     std::vector<int> cands = {kFixedE};
     if (ctx->opt.autotune) {
-      cands = {4, 8, 16};
+      cands = {8, 16, 32};
       if (longest <= 256) cands.insert(cands.end(), {-4, -8});
     }
     DevSched best = on_a ? ctx->sa8 : ctx->st8;
@@ -887,7 +887,7 @@ static pdhg_status tune_batch_schedules(pdhg_ctx* ctx) {
         lpt = on_a ? ctx->lp_a8_tiles : ctx->lp_t8_tiles;
       } else {
         HostSched h = build_sched(rp.data(), nrows, e, off, count);
-        CKS(upload_sched(ctx, h, &d));
+        CKS(upload_sched(ctx, h, &d, on_a ? ctx->a_rp : ctx->t_rp));
         CKS(dalloc(ctx, &lpt, (size_t)count + 1));
         CK(cudaMemcpyAsync(lpt, h.lp_tiles.data(), sizeof(int32_t) * (count + 1),
                            cudaMemcpyHostToDevice, ctx->stream));

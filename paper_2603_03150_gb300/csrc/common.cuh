@@ -9,10 +9,11 @@ constexpr int kWarp = 32;
 
 // ---------------------------------------------------------------------------
 // CSR tile schedule.  A tile is a run of whole rows whose nonzeros fit in
-// `tile_nnz`, or one chunk of a row longer than that ("split row").  A split
-// row's chunks form a group: each chunk writes its partial sum to a slot, and
-// the chunk that arrives last (atomic ticket) adds the slots in chunk order
-// and runs the row epilogue, so the sum order is fixed.
+// `tile_nnz`, one chunk of a row longer than that ("split row"), or a run of
+// rows without nonzeros (nz_begin == nz_end).  A split row's chunks form a
+// group: each chunk writes its partial sum to a slot, and the chunk that
+// arrives last (atomic ticket) adds the slots in chunk order and runs the row
+// epilogue, so the sum order is fixed.
 // ---------------------------------------------------------------------------
 struct Tile {
   int32_t row_begin, row_end;  // rows [row_begin, row_end)
@@ -20,7 +21,7 @@ struct Tile {
   int32_t split;               // -1: whole rows; else split-group index
   int32_t part;                // chunk index within the split group
   int32_t lp;                  // LP of the tile's rows (batched solves; 0 otherwise)
-  int32_t pad;
+  int32_t word0;               // segmented schedules: first window word of the tile
 };
 
 struct SplitGroup {
@@ -35,6 +36,7 @@ struct SchedView {
   const SplitGroup* groups;
   int32_t* counters;  // [ngroups], zero between launches
   void* slots;        // [total parts * NV] partial sums
+  const void* wd;      // window words of the whole-row tiles (segmented schedules)
   int32_t ntiles;
   int32_t tile_nnz;  // nonzero capacity of a tile (block * e - 4)
   int32_t max_rows;  // rows per tile at most
@@ -113,12 +115,66 @@ __device__ __forceinline__ void block_sum(const double (&v)[NQ], double (&out)[N
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Loads of the matrix stream (column indices, values, window words): read
+// once per SpMV, so they carry an L2 evict-first policy and skip L1, leaving
+// both caches to the gathered vector and the per-row operands.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t stream_policy() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ int4 ld_stream_int4(const int32_t* p, uint64_t pol) {
+  int4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t pol) {
+  uint32_t r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t ld_stream(const uint64_t* p, uint64_t pol) {
+  uint64_t r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
+  int32_t r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
+  float r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
+  double r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
   float v[4];
   __device__ __forceinline__ void load(const float* p) {
     float4 t = __ldg(reinterpret_cast<const float4*>(p));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ __forceinline__ void load_stream(const float* p, uint64_t pol) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+        : "l"(p), "l"(pol));
   }
   __device__ __forceinline__ void store_smem(float* p) const {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
@@ -130,6 +186,14 @@ template <> struct Vec4<double> {
     double2 a = __ldg(reinterpret_cast<const double2*>(p));
     double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ __forceinline__ void load_stream(const double* p, uint64_t pol) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+        : "=d"(v[0]), "=d"(v[1])
+        : "l"(p), "l"(pol));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+        : "=d"(v[2]), "=d"(v[3])
+        : "l"(p + 2), "l"(pol));
   }
   __device__ __forceinline__ void store_smem(double* p) const {
     reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);

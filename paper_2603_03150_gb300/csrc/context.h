@@ -38,11 +38,13 @@ struct HostSched {
   std::vector<SplitGroup> groups;
   int total_parts = 0;
   int tile_nnz = 0, max_rows = 0, e = 8;
+  int64_t nwords = 0;             // window words of the whole-row tiles (e > 0)
   std::vector<int32_t> lp_tiles;  // [count + 1] first tile of each LP
 };
 
 // Tiles of whole rows (at most tile_capacity(kBlock, e) nonzeros and
-// tile_max_rows(kBlock) rows) or capacity-sized chunks of a longer row.
+// tile_max_rows(kBlock) rows, none of them empty), capacity-sized chunks of a
+// longer row, or runs of empty rows.
 // With lp_off (count + 1 row offsets) no tile crosses an LP boundary and each
 // tile records its LP.
 HostSched build_sched(const int32_t* rp, int nrows, int e, const int64_t* lp_off = nullptr,
@@ -53,6 +55,7 @@ struct DevSched {
   SplitGroup* groups = nullptr;
   int32_t* counters = nullptr;
   double* slots = nullptr;
+  uint32_t* wd = nullptr;
   SchedView view{};
 };
 
@@ -151,7 +154,9 @@ pdhg_status copy_in(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes);
 pdhg_status copy_out(pdhg_ctx* ctx, void* dst, const void* src, size_t bytes);
 // kind 0: one gathered vector in the iteration precision, 1: two, 2: one in float64
 size_t smem_for(int kind, bool mixed, int max_rows, int e);
-pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d);
+// copies the schedule to the device and computes its window words from the
+// device row pointer rp of the same matrix
+pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d, const int32_t* rp);
 Launch make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int ntiles);
 size_t elem(const pdhg_ctx* ctx);
 // mean duration of a plain SpMV over schedule d (A when on_a, else A^T)

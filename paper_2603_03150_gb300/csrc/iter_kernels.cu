@@ -222,8 +222,8 @@ __global__ void k_restart(IterBuffers<T> B) {
       constexpr int E_ = -8;                    \
       __VA_ARGS__;                              \
     } break;                                    \
-    case 4: {                                   \
-      constexpr int E_ = 4;                     \
+    case 32: {                                  \
+      constexpr int E_ = 32;                    \
       __VA_ARGS__;                              \
     } break;                                    \
     case 16: {                                  \
@@ -606,7 +606,7 @@ static const void* fixed_kernel(int which) {
 cudaError_t configure_tile_kernels(size_t max_smem) {
   cudaError_t e = cudaSuccess;
   for (int w = 0; w < 8; ++w)
-    for (const void* f : {tile_kernel<4>(w), tile_kernel<8>(w), tile_kernel<16>(w),
+    for (const void* f : {tile_kernel<8>(w), tile_kernel<16>(w), tile_kernel<32>(w),
                           tile_kernel<-4>(w), tile_kernel<-8>(w)}) {
       cudaError_t r = set_max_dyn(f, max_smem);
       if (r != cudaSuccess) e = r;
@@ -624,8 +624,8 @@ int tile_occupancy(int which, int e, size_t smem) {
   const void* f = nullptr;
   if (which >= 8)
     f = fixed_kernel(0);
-  else if (e == 4)
-    f = tile_kernel<4>(which);
+  else if (e == 32)
+    f = tile_kernel<32>(which);
   else if (e == -4)
     f = tile_kernel<-4>(which);
   else if (e == -8)

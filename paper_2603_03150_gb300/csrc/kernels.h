@@ -92,6 +92,11 @@ void launch_scatter(int m, const int32_t* rp, const int32_t* col, const double* 
 void launch_segsort(int nseg, const int32_t* seg_ptr, int32_t* keys, double* vals,
                     const int32_t* long_ids, int n_long, int32_t* tmp_k, double* tmp_v,
                     cudaStream_t s);
+// window words of the whole-row tiles of a segmented schedule (e = 8, 16 or
+// 32 nonzeros per thread; 64-bit words for 32) over the matrix with device
+// row pointer rp
+void launch_window_words(const Tile* tiles, int ntiles, const int32_t* rp, int e, uint32_t* wd,
+                         cudaStream_t s);
 // Ruiz / Pock-Chambolle statistic of each row of D_self M D_other:
 // mode 0: sqrt(max |.|), mode 1: sqrt(sum |.|); zero -> 1.
 void launch_row_stat(int nrows, const int32_t* rp, const int32_t* col, const double* val,

@@ -517,4 +517,54 @@ cudaError_t configure_setup_kernels(size_t max_smem) {
   return e;
 }
 
+// ---------------------------------------------------------------------------
+// window words of a segmented schedule: one thread per (whole-row tile,
+// thread window); the row of the window's first nonzero by binary search over
+// the tile's rows, then the row ends inside the window
+// ---------------------------------------------------------------------------
+template <int E>
+__global__ void k_window_words(const Tile* __restrict__ tiles, int ntiles,
+                               const int32_t* __restrict__ rp,
+                               typename WindowWord<E>::type* __restrict__ wd) {
+  constexpr int e = E;
+  const int64_t total = (int64_t)ntiles * kBlock;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(idx / kBlock), th = (int)(idx % kBlock);
+    const Tile tl = tiles[t];
+    if (tl.split >= 0 || tl.nz_begin == tl.nz_end) continue;
+    const int w0 = (tl.nz_begin & ~3) + th * e;
+    const int k0 = max(w0, tl.nz_begin), k1 = min(w0 + e, tl.nz_end);
+    typename WindowWord<E>::type word = 0;
+    if (k0 < k1) {
+      int lo = tl.row_begin, hi = tl.row_end;  // rp[lo] <= k0 < rp[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rp[mid] <= k0) lo = mid; else hi = mid;
+      }
+      uint64_t mask = 0;
+      int r = lo, next_end = rp[lo + 1];
+      for (int k = k0; k < k1; ++k)
+        if (k + 1 == next_end) {
+          mask |= 1ull << (k - w0);
+          if (++r < tl.row_end) next_end = rp[r + 1];
+        }
+      word = window_word<E>(lo - tl.row_begin, rp[lo] < k0, mask);
+    }
+    wd[tl.word0 + th] = word;
+  }
+}
+
+void launch_window_words(const Tile* tiles, int ntiles, const int32_t* rp, int e, uint32_t* wd,
+                         cudaStream_t s) {
+  if (ntiles <= 0) return;
+  const int g = grid_cap((int64_t)ntiles * kBlock);
+  if (e == 32)
+    k_window_words<32><<<g, 256, 0, s>>>(tiles, ntiles, rp, reinterpret_cast<uint64_t*>(wd));
+  else if (e == 16)
+    k_window_words<16><<<g, 256, 0, s>>>(tiles, ntiles, rp, wd);
+  else
+    k_window_words<8><<<g, 256, 0, s>>>(tiles, ntiles, rp, wd);
+}
+
 }  // namespace pdhg

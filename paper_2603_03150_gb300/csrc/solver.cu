@@ -82,14 +82,22 @@ HostSched build_sched(const int32_t* rp, int nrows, int e, const int64_t* lp_off
       continue;
     }
     const int start = r;
+    if (len == 0) {  // a run of rows without nonzeros
+      while (r < nrows && r < lp_end && r - start < h.max_rows && rp[r + 1] == rp[r]) ++r;
+      h.tiles.push_back(Tile{start, r, rp[start], rp[start], -1, 0, lp, 0});
+      continue;
+    }
     int64_t nz = 0;
     while (r < nrows && r < lp_end && r - start < h.max_rows) {
       const int64_t l = (int64_t)rp[r + 1] - rp[r];
-      if (l > cap || nz + l > cap) break;
+      if (l == 0 || l > cap || nz + l > cap) break;
       nz += l;
       ++r;
     }
-    h.tiles.push_back(Tile{start, r, rp[start], rp[r], -1, 0, lp, 0});
+    // whole rows: one window word per thread (segmented schedules)
+    const int32_t word0 = e > 0 ? (int32_t)h.nwords : 0;
+    if (e > 0) h.nwords += kBlock;
+    h.tiles.push_back(Tile{start, r, rp[start], rp[r], -1, 0, lp, word0});
   }
   // LPs with no rows left (none with m >= 1) still get a range
   while ((int)h.lp_tiles.size() < count) h.lp_tiles.push_back((int32_t)h.tiles.size());
@@ -124,12 +132,19 @@ size_t pdhg::smem_for(int kind, bool mixed, int max_rows, int e) {
   return tile_smem(1, false, max_rows, e);
 }
 
-pdhg_status pdhg::upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) {
+pdhg_status pdhg::upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d,
+                               const int32_t* rp) {
   *d = DevSched{};
+  if (h.nwords >= (int64_t)1 << 31) {
+    set_error("tile schedule too large (%lld window words)", (long long)h.nwords);
+    return PDHG_INVALID_ARG;
+  }
   CKS(dalloc(ctx, &d->tiles, h.tiles.size()));
   CKS(dalloc(ctx, &d->groups, h.groups.size()));
   CKS(dalloc(ctx, &d->counters, h.groups.size()));
   CKS(dalloc(ctx, &d->slots, (size_t)h.total_parts * 2));
+  // 32-bit words up to 16 nonzeros per thread, 64-bit words beyond
+  CKS(dalloc(ctx, &d->wd, (size_t)h.nwords * (h.e > 16 ? 2 : 1)));
   if (!h.tiles.empty())
     CK(cudaMemcpyAsync(d->tiles, h.tiles.data(), h.tiles.size() * sizeof(Tile),
                        cudaMemcpyHostToDevice, ctx->stream));
@@ -138,10 +153,15 @@ pdhg_status pdhg::upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) {
                        cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemsetAsync(d->counters, 0, std::max<size_t>(h.groups.size(), 1) * sizeof(int32_t),
                      ctx->stream));
+  if (h.nwords > 0) {
+    launch_window_words(d->tiles, (int)h.tiles.size(), rp, h.e, d->wd, ctx->stream);
+    ctx->launches += 1;
+  }
   d->view.tiles = d->tiles;
   d->view.groups = d->groups;
   d->view.counters = d->counters;
   d->view.slots = d->slots;
+  d->view.wd = d->wd;
   d->view.ntiles = (int32_t)h.tiles.size();
   d->view.tile_nnz = h.tile_nnz;
   d->view.max_rows = h.max_rows;
@@ -149,6 +169,7 @@ pdhg_status pdhg::upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d) {
   d->view.e = h.e;
   // make the host vectors' lifetime irrelevant: copies are enqueued, wait here
   CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
   return PDHG_OK;
 }
 
@@ -205,8 +226,8 @@ static pdhg_status fixed_schedules(pdhg_ctx* ctx) {
     const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
     const int nrows = on_a ? ctx->m : ctx->n;
     HostSched h = build_sched(rp.data(), nrows, kFixedE);
-    CKS(upload_sched(ctx, h, on_a ? &ctx->sa8 : &ctx->st8));
-    for (int r = 0; r < nrows; ++r) long_rows += (rp[r + 1] - rp[r]) > tile_capacity(kBlock, 4);
+    CKS(upload_sched(ctx, h, on_a ? &ctx->sa8 : &ctx->st8, on_a ? ctx->a_rp : ctx->t_rp));
+    for (int r = 0; r < nrows; ++r) long_rows += (rp[r + 1] - rp[r]) > tile_capacity(kBlock, 8);
   }
   const bool mx = ctx->mixed;
   const SchedView &A8 = ctx->sa8.view, &T8 = ctx->st8.view;
@@ -337,9 +358,9 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
     if (ctx->opt.tile_nnz < 0)  // forced vector variant (only where rows are short)
       cands.push_back(longest <= 256 ? (ctx->opt.tile_nnz <= -8 ? -8 : -4) : 8);
     else if (ctx->opt.tile_nnz > 0)
-      cands.push_back(ctx->opt.tile_nnz <= 1024 ? 4 : (ctx->opt.tile_nnz <= 2048 ? 8 : 16));
+      cands.push_back(ctx->opt.tile_nnz <= 2048 ? 8 : (ctx->opt.tile_nnz <= 4096 ? 16 : 32));
     else if (ctx->opt.autotune) {
-      cands = {4, 8, 16};
+      cands = {8, 16, 32};
       if (longest <= 256) cands.insert(cands.end(), {-4, -8});
     } else {
       cands = {8};
@@ -352,7 +373,7 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
         d = on_a ? ctx->sa8 : ctx->st8;
       } else {
         HostSched h = build_sched(rp.data(), nrows, e);
-        CKS(upload_sched(ctx, h, &d));
+        CKS(upload_sched(ctx, h, &d, on_a ? ctx->a_rp : ctx->t_rp));
       }
       (on_a ? ctx->sa : ctx->st) = d;
       if (on_a)

@@ -1,15 +1,17 @@
 // Tiled CSR SpMV core shared by every kernel that multiplies by A~ or A~^T.
 //
 // A tile is a run of whole rows holding at most BLOCK*E - 4 nonzeros, or one
-// chunk of a row too long for a tile ("split row").  Per tile:
+// chunk of a row too long for a tile ("split row"), or a run of rows without
+// nonzeros.  Per tile of whole rows:
 //  (1) thread t loads the E consecutive nonzeros of the window
 //      [a + tE, a + tE + E), a = the tile start rounded down to 16 bytes,
 //      with 128-bit loads of column indices and values, and issues all E
 //      gathers v[col] back to back (products stay in registers);
-//  (2) the thread walks the row boundaries inside its window: rows that end
-//      there are finished at once, the first one with a carry-in if it began
-//      in an earlier window, and the row still open at the window's end is
-//      carried out;
+//  (2) the thread walks the row ends inside its window, read from a 32-bit
+//      window word computed once with the schedule (row-end mask, first row,
+//      "continues a row" bit): rows that end there are finished at once, the
+//      first one with a carry-in if it began in an earlier window, and the row
+//      still open at the window's end is carried out;
 //  (3) carries are combined by a segmented scan over threads (warp shuffles,
 //      then across warps in shared memory), so every thread does the same
 //      amount of work whatever the row lengths;
@@ -19,6 +21,8 @@
 // chunk that arrives last (atomic ticket) adds the slots in chunk order and
 // runs the row epilogue, so the sum order is fixed.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pdhg {
@@ -34,16 +38,6 @@ __host__ __device__ constexpr int tile_capacity(int block, int e) { return block
 
 // Rows a tile may hold (bounds the staged row sums in shared memory).
 __host__ __device__ constexpr int tile_max_rows(int block) { return block * 4; }
-
-// Shared memory bytes needed by run_tiles for a schedule.
-template <typename T, int NV, int BLOCK>
-__host__ __device__ constexpr size_t tile_smem_bytes(int max_rows) {
-  return sizeof(int32_t) * (size_t)(max_rows + 4)   // row offsets of the tile
-         + sizeof(T) * (size_t)NV * (max_rows + 4)  // staged row sums
-         + sizeof(int32_t) * 2 * (BLOCK / 32)       // first/last key per warp
-         + sizeof(T) * (size_t)NV * (BLOCK / 32)    // last value per warp
-         + 64;
-}
 
 // Epilogue concept:  __device__ void row(int r, const T (&s)[NV], int split_group)
 // split_group < 0 for rows completed inside one tile; otherwise the index of
@@ -65,216 +59,272 @@ __device__ __forceinline__ auto epi_end(Epi& e, const Tile& t, int i, int) -> de
 }
 template <class Epi>
 __device__ __forceinline__ void epi_end(Epi&, const Tile&, int, long) {}
+
+// One chunk of a split row: block sum of the threads' partial sums (each the
+// sum of its window's products in nonzero order), then the ordered slot
+// combine (the chunk that arrives last adds the slots in chunk order and runs
+// the row epilogue).  Ends with a block barrier.
+template <typename T, int NV, int BLOCK, class Epi>
+__device__ __forceinline__ void split_chunk(const SchedView& S, const Tile& tl,
+                                            const T (&part_in)[NV], Epi& epi, T* wsum) {
+  constexpr int NW = BLOCK / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const T sv = warp_sum(part_in[v]);
+    if (lane == 0) wsum[v * NW + warp] = sv;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    T part[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      part[v] = T(0);
+      for (int w = 0; w < NW; ++w) part[v] += wsum[v * NW + w];
+    }
+    T* slots = reinterpret_cast<T*>(S.slots);
+    const SplitGroup grp = S.groups[tl.split];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) slots[(size_t)(grp.slot0 + tl.part) * NV + v] = part[v];
+    __threadfence();
+    const int prev = atomicAdd(S.counters + tl.split, 1);
+    if (prev == grp.nparts - 1) {
+      __threadfence();
+      T tot[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) tot[v] = T(0);
+      for (int pp = 0; pp < grp.nparts; ++pp)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) tot[v] += __ldcg(slots + (size_t)(grp.slot0 + pp) * NV + v);
+      S.counters[tl.split] = 0;
+      epi.row(grp.row, tot, tl.split);
+    }
+  }
+  __syncthreads();
+}
+
+// Combines the open carries of a whole-row tile.  Each thread passes the row
+// whose sum is still open at the end of its window (key, -1 if none) with its
+// partial sum acc, and the row it closed first if that row began before its
+// window (head_row, -1 if none) with the partial sum head_val; the carries of
+// equal keys are added by a segmented scan over threads in thread order and
+// the head rows are written to rsum.  Ends with a barrier.
+template <typename T, int NV, int BLOCK>
+__device__ __forceinline__ void carry_combine(int key, const T (&acc)[NV], int head_row,
+                                              T (&head_val)[NV], T* rsum, int rstride,
+                                              int32_t* wfirst, int32_t* wlast, T* wsum) {
+  constexpr int NW = BLOCK / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // segmented inclusive scan of the open carries over threads
+  T sv[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sv[v] = (key >= 0) ? acc[v] : T(0);
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int ko = __shfl_up_sync(0xffffffffu, key, off);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T o = __shfl_up_sync(0xffffffffu, sv[v], off);
+      if (lane >= off && ko == key) sv[v] += o;
+    }
+  }
+  const unsigned same = __match_any_sync(0xffffffffu, key);
+  if (lane == 31) {
+    wlast[warp] = key;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) wsum[v * NW + warp] = sv[v];
+  }
+  if (lane == 0) wfirst[warp] = key;
+  __syncthreads();
+  if (key >= 0 && (same & 1u)) {  // this run reaches back to lane 0
+    for (int w = warp - 1; w >= 0; --w) {
+      if (wlast[w] != key) break;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sv[v] += wsum[v * NW + w];
+      if (wfirst[w] != key) break;
+    }
+  }
+  // carry-in of a row that began before this window: the previous thread's
+  // scan value when it carries the same row (from the previous warp for lane 0)
+  const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+  T cprev[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) cprev[v] = __shfl_up_sync(0xffffffffu, sv[v], 1);
+  if (head_row >= 0) {
+    if (lane > 0) {
+      if (kprev == head_row)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) head_val[v] += cprev[v];
+    } else {
+      for (int w = warp - 1; w >= 0; --w) {
+        if (wlast[w] != head_row) break;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) head_val[v] += wsum[v * NW + w];
+        if (wfirst[w] != head_row) break;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) rsum[v * rstride + head_row] = head_val[v];
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Window words.  The row structure of every thread window of a whole-row
+// tile is computed once when the schedule is built (one word per window;
+// tile.word0 = index of the tile's first word, schedule view .wd).  With
+// M = 16 mask bits (32-bit words, E <= 16) or M = 32 (64-bit words, E = 32):
+//   bits 0..M-1   row-end mask: bit e set when nonzero w0+e is its row's last
+//   bit  M        the window's first nonzero continues a row begun before it
+//   bits M+1..    row of the window's first nonzero, relative to row_begin
+// Tiles of whole rows hold no row without nonzeros (such rows form tiles of
+// their own, nz_begin == nz_end), so the walk is one mask test per nonzero.
+// ---------------------------------------------------------------------------
+template <int E>
+struct WindowWord {
+  using type = typename std::conditional<(E > 16), uint64_t, uint32_t>::type;
+  static constexpr int kMaskBits = E > 16 ? 32 : 16;
+};
+
+template <int E>
+__host__ __device__ constexpr typename WindowWord<E>::type window_word(int first_row, bool head,
+                                                                       uint64_t mask) {
+  using W = typename WindowWord<E>::type;
+  return ((W)first_row << (WindowWord<E>::kMaskBits + 1)) |
+         ((W)(head ? 1u : 0u) << WindowWord<E>::kMaskBits) | (W)mask;
+}
+
+// Segmented tile SpMV (row_ptr is not read: the window words carry the rows).
+// A thread's window of E nonzeros is loaded, gathered and walked in steps of
+// EC = 8 (E = 16, 32: the per-tile work - descriptor, carry scan, barriers -
+// is shared by more nonzeros at the register cost of E = 8).
 template <typename T, int NV, int BLOCK, int E, class Epi>
-__device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __restrict__ row_ptr,
+__device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __restrict__ /*row_ptr*/,
                                           const int32_t* __restrict__ col,
                                           const T* __restrict__ val, const Gather<T, NV>& g,
                                           Epi& epi, unsigned char* smem) {
-  static_assert(E % 4 == 0, "E must be a multiple of 4");
+  static_assert(E % 4 == 0 && E <= 32, "E must be a multiple of 4, at most 32");
+  using W = typename WindowWord<E>::type;
+  constexpr int MB = WindowWord<E>::kMaskBits;
+  constexpr int EC = E < 8 ? E : 8;
   constexpr int NW = BLOCK / 32;
   const int rstride = S.max_rows + 4;
-  int32_t* rps = reinterpret_cast<int32_t*>(smem);
-  int32_t* wfirst = rps + rstride;
+  int32_t* wfirst = reinterpret_cast<int32_t*>(smem);
   int32_t* wlast = wfirst + NW;
   T* rsum = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(wlast + NW) + 15) & ~uintptr_t(15));
   T* wsum = rsum + NV * rstride;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
+  const W* __restrict__ wd = reinterpret_cast<const W*>(S.wd);
+  const uint64_t pol = stream_policy();
 
   for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
     const Tile tl = S.tiles[t];
     if (!epi_begin(epi, tl, 0)) continue;
     const int nzb = tl.nz_begin, nze = tl.nz_end;
-    const int w0 = (nzb & ~3) + tid * E;
-
-    // (1) loads and gathers
-    int cidx[E];
-    T vv[E];
+    const int nrows = tl.row_end - tl.row_begin;
+    if (nzb == nze) {  // rows without nonzeros: zero sums
+      T z[NV];
 #pragma unroll
-    for (int q = 0; q < E / 4; ++q) {
-      const int k4 = w0 + 4 * q;
-      if (k4 < nze) {
-        const int4 c4 = ldg_int4(col + k4);
-        Vec4<T> v4;
-        v4.load(val + k4);
-        cidx[4 * q + 0] = c4.x;
-        cidx[4 * q + 1] = c4.y;
-        cidx[4 * q + 2] = c4.z;
-        cidx[4 * q + 3] = c4.w;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) vv[4 * q + e] = v4.v[e];
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          cidx[4 * q + e] = 0;
-          vv[4 * q + e] = T(0);
-        }
-      }
-    }
-    T p[NV][E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int k = w0 + e;
-      const bool in = k >= nzb && k < nze;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) p[v][e] = in ? vv[e] * __ldg(g.v[v] + cidx[e]) : T(0);
-    }
-
-    if (tl.split >= 0) {
-      // one chunk of a long row: block sum, then the ordered slot combine
-      T s[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        s[v] = T(0);
-#pragma unroll
-        for (int e = 0; e < E; ++e) s[v] += p[v][e];
-        s[v] = warp_sum(s[v]);
-        if (lane == 0) wsum[v * NW + warp] = s[v];
-      }
-      __syncthreads();
-      if (tid == 0) {
-        T part[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          part[v] = T(0);
-          for (int w = 0; w < NW; ++w) part[v] += wsum[v * NW + w];
-        }
-        T* slots = reinterpret_cast<T*>(S.slots);
-        const SplitGroup grp = S.groups[tl.split];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) slots[(size_t)(grp.slot0 + tl.part) * NV + v] = part[v];
-        __threadfence();
-        const int prev = atomicAdd(S.counters + tl.split, 1);
-        if (prev == grp.nparts - 1) {
-          __threadfence();
-          T tot[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) tot[v] = T(0);
-          for (int pp = 0; pp < grp.nparts; ++pp)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) tot[v] += __ldcg(slots + (size_t)(grp.slot0 + pp) * NV + v);
-          S.counters[tl.split] = 0;
-          epi.row(grp.row, tot, tl.split);
-        }
-      }
+      for (int v = 0; v < NV; ++v) z[v] = T(0);
+      for (int r = tid; r < nrows; r += BLOCK) epi.row(tl.row_begin + r, z, -1);
       __syncthreads();
       epi_end(epi, tl, t, 0);
       continue;
     }
+    const int w0 = (nzb & ~3) + tid * E;
+    const W d = tl.split < 0 ? ld_stream(wd + tl.word0 + tid, pol) : W(0);
 
-    // row offsets of the tile (absolute nonzero positions)
-    const int nrows = tl.row_end - tl.row_begin;
-    for (int r = tid; r <= nrows; r += BLOCK) rps[r] = __ldg(row_ptr + tl.row_begin + r);
-    __syncthreads();
-
-    // (2) walk the row ends inside this thread's window
-    const int k0 = max(w0, nzb), k1 = min(w0 + E, nze);
-    int key = -1, head_row = -1;
+    // load, gather and walk; products outside [nzb, nze) are zero and carry
+    // no mask bit (split chunks have no mask bits: acc is the window's sum)
+    int r = (int)(d >> (MB + 1));
+    bool head = (d >> MB) & 1u;
+    int head_row = -1;
     T acc[NV], head_val[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = head_val[v] = T(0);
-    if (k0 < k1) {
-      // row holding k0: the last r with rps[r] <= k0 (skips empty rows)
-      int lo = 0, hi = nrows;  // invariant: rps[lo] <= k0 < rps[hi]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (rps[mid] <= k0) lo = mid; else hi = mid;
-      }
-      int r = lo;
-      int next_end = rps[r + 1];
-      bool open = false, first = true;
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int k = w0 + e;
-        if (k >= k0 && k < k1) {
+    for (int c = 0; c < E / EC; ++c) {
+      const int wc = w0 + c * EC;
+      if (wc >= nze) break;
+      int cidx[EC];
+      T vv[EC];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) acc[v] += p[v][e];
-          open = true;
-          if (k + 1 == next_end) {
-            if (first && rps[r] < k0) {
-              head_row = r;
+      for (int q = 0; q < EC / 4; ++q) {
+        const int k4 = wc + 4 * q;
+        if (k4 < nze) {
+          const int4 c4 = ld_stream_int4(col + k4, pol);
+          Vec4<T> v4;
+          v4.load_stream(val + k4, pol);
+          cidx[4 * q + 0] = c4.x;
+          cidx[4 * q + 1] = c4.y;
+          cidx[4 * q + 2] = c4.z;
+          cidx[4 * q + 3] = c4.w;
 #pragma unroll
-              for (int v = 0; v < NV; ++v) head_val[v] = acc[v];
-            } else {
+          for (int e = 0; e < 4; ++e) vv[4 * q + e] = v4.v[e];
+        } else {
 #pragma unroll
-              for (int v = 0; v < NV; ++v) rsum[v * rstride + r] = acc[v];
-            }
-            first = false;
-            open = false;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] = T(0);
-            ++r;
-            while (r < nrows && rps[r + 1] == rps[r]) ++r;
-            next_end = (r < nrows) ? rps[r + 1] : 0x7fffffff;
+          for (int e = 0; e < 4; ++e) {
+            cidx[4 * q + e] = 0;
+            vv[4 * q + e] = T(0);
           }
         }
       }
-      if (open) key = r;
-    }
-
-    // (3) segmented inclusive scan of the open carries over threads
-    T sv[NV];
+      T p[NV][EC];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sv[v] = (key >= 0) ? acc[v] : T(0);
+      for (int e = 0; e < EC; ++e) {
+        const int k = wc + e;
+        const bool in = k >= nzb && k < nze;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int ko = __shfl_up_sync(0xffffffffu, key, off);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const T o = __shfl_up_sync(0xffffffffu, sv[v], off);
-        if (lane >= off && ko == key) sv[v] += o;
+        for (int v = 0; v < NV; ++v) p[v][e] = in ? vv[e] * __ldg(g.v[v] + cidx[e]) : T(0);
       }
-    }
-    const unsigned same = __match_any_sync(0xffffffffu, key);
-    if (lane == 31) {
-      wlast[warp] = key;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) wsum[v * NW + warp] = sv[v];
-    }
-    if (lane == 0) wfirst[warp] = key;
-    __syncthreads();
-    if (key >= 0 && (same & 1u)) {  // this run reaches back to lane 0
-      for (int w = warp - 1; w >= 0; --w) {
-        if (wlast[w] != key) break;
+      for (int e = 0; e < EC; ++e) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sv[v] += wsum[v * NW + w];
-        if (wfirst[w] != key) break;
-      }
-    }
-    // carry-in of a row that began before this window: the previous thread's
-    // scan value when it carries the same row (from the previous warp for lane 0)
-    const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-    T cprev[NV];
+        for (int v = 0; v < NV; ++v) acc[v] += p[v][e];
+        if ((d >> (c * EC + e)) & 1u) {
+          if (head) {
+            head_row = r;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) cprev[v] = __shfl_up_sync(0xffffffffu, sv[v], 1);
-    if (head_row >= 0) {
-      if (lane > 0) {
-        if (kprev == head_row)
+            for (int v = 0; v < NV; ++v) head_val[v] = acc[v];
+          } else {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) head_val[v] += cprev[v];
-      } else {
-        for (int w = warp - 1; w >= 0; --w) {
-          if (wlast[w] != head_row) break;
+            for (int v = 0; v < NV; ++v) rsum[v * rstride + r] = acc[v];
+          }
+          head = false;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) head_val[v] += wsum[v * NW + w];
-          if (wfirst[w] != head_row) break;
+          for (int v = 0; v < NV; ++v) acc[v] = T(0);
+          ++r;
         }
       }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) rsum[v * rstride + head_row] = head_val[v];
     }
-    __syncthreads();
 
-    // (4) epilogue, one coalesced pass over the tile's rows
-    for (int r = tid; r < nrows; r += BLOCK) {
-      T s[NV];
-      const bool empty = rps[r] == rps[r + 1];
+    if (tl.split >= 0) {
+      split_chunk<T, NV, BLOCK>(S, tl, acc, epi, wsum);
+      epi_end(epi, tl, t, 0);
+      continue;
+    }
+
+    // the row still open at the window's end is carried out
+    const int k0 = max(w0, nzb), k1 = min(w0 + E, nze);
+    const int key = (k0 < k1 && !((d >> (k1 - 1 - w0)) & 1u)) ? r : -1;
+    carry_combine<T, NV, BLOCK>(key, acc, head_row, head_val, rsum, rstride, wfirst, wlast, wsum);
+
+    for (int rr = tid; rr < nrows; rr += BLOCK) {
+      T sr[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) s[v] = empty ? T(0) : rsum[v * rstride + r];
-      epi.row(tl.row_begin + r, s, -1);
+      for (int v = 0; v < NV; ++v) sr[v] = rsum[v * rstride + rr];
+      epi.row(tl.row_begin + rr, sr, -1);
     }
     __syncthreads();
     epi_end(epi, tl, t, 0);
   }
+}
+
+// Shared memory bytes needed by run_tiles for a schedule.
+template <typename T, int NV, int BLOCK>
+__host__ __device__ constexpr size_t tile_smem_bytes(int max_rows) {
+  return sizeof(int32_t) * 2 * (BLOCK / 32) + 16 + sizeof(T) * (size_t)NV * (max_rows + 4) +
+         sizeof(T) * (size_t)NV * (BLOCK / 32) + 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -296,6 +346,7 @@ __device__ __forceinline__ void run_tiles_vec(const SchedView& S, const int32_t*
   T* rsum = reinterpret_cast<T*>(smem);
   T* wsum = rsum + NV * rstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t pol = stream_policy();
   const int grp = tid / G, gl = tid & (G - 1);
   constexpr int NG = BLOCK / G;
   for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
@@ -306,8 +357,8 @@ __device__ __forceinline__ void run_tiles_vec(const SchedView& S, const int32_t*
 #pragma unroll
       for (int v = 0; v < NV; ++v) s[v] = T(0);
       for (int k = tl.nz_begin + tid; k < tl.nz_end; k += BLOCK) {
-        const T a = __ldg(val + k);
-        const int c = __ldg(col + k);
+        const T a = ld_stream(val + k, pol);
+        const int c = ld_stream(col + k, pol);
 #pragma unroll
         for (int v = 0; v < NV; ++v) s[v] += a * __ldg(g.v[v] + c);
       }
@@ -356,8 +407,8 @@ __device__ __forceinline__ void run_tiles_vec(const SchedView& S, const int32_t*
       if (r0 + grp < nrows) {
         const int e = __ldg(row_ptr + r + 1);
         for (int k = __ldg(row_ptr + r) + gl; k < e; k += G) {
-          const T a = __ldg(val + k);
-          const int c = __ldg(col + k);
+          const T a = ld_stream(val + k, pol);
+          const int c = ld_stream(col + k, pol);
 #pragma unroll
           for (int v = 0; v < NV; ++v) s[v] += a * __ldg(g.v[v] + c);
         }
