@@ -290,7 +290,7 @@ def run_ours(args):
                 "frac": round(ach / peak, 4),
                 "traffic": ncu_traffic("k_primal" if dom == "primal" else "k_dual", args.precision,
                                        args.workload,
-                                       (rec[0]["sched"]["at_tile_nnz" if dom == "primal" else "a_tile_nnz"] + 4) // 256),
+                                       rec[0]["sched"]["at_variant" if dom == "primal" else "a_variant"]),
                 "kernel": "k_primal" if dom == "primal" else "k_dual",
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": ab[dom],
                 "mean_launch_ms": round(dur, 5), "samples": ns,

@@ -72,12 +72,12 @@ typedef struct pdhg_options {
   int32_t use_graphs;      /* 1 (default): replay each F-iteration chunk as a
                               CUDA graph                                        */
   int32_t autotune;        /* 1 (default): time SpMV tile schedules at create   */
-  int32_t tile_nnz;        /* 0: autotune; > 0: segmented SpMV tiles of up to
-                              2044 (tile_nnz <= 2048), 4092 (<= 4096) or 8188
-                              nonzeros (8 / 16 / 32 per thread); -4 / -8: the
-                              vector SpMV with 4 / 8 lanes per row (matrices
-                              whose rows all have <= 256 nonzeros; others fall
-                              back to segmented)                               */
+  int32_t tile_nnz;        /* 0: autotune; > 0: segmented SpMV tiles of at most
+                              tile_nnz nonzeros, walked with 8 (tile_nnz <=
+                              2044), 16 (<= 4092) or 32 nonzeros per thread;
+                              -4 / -8: the vector SpMV with 4 / 8 lanes per row
+                              (matrices whose rows all have <= 256 nonzeros;
+                              others fall back to segmented)                   */
   int32_t kernel_timing;   /* 1: sample primal/dual kernel durations with CUDA
                               events during pdhg_solve                          */
   int32_t verbose;
@@ -166,11 +166,13 @@ pdhg_status pdhg_get_log(pdhg_ctx* ctx, int32_t cap, int32_t* count, int64_t* k,
 pdhg_status pdhg_get_kernel_timing(pdhg_ctx* ctx, double* primal_ms, double* dual_ms,
                                    int64_t* samples);
 
-/* Tile schedule picked for A (dual kernel) and A^T (primal kernel):
- * nonzeros per tile, threads per block, tiles, grid size.  */
+/* Tile schedule picked for A (dual kernel) and A^T (primal kernel): nonzeros
+ * per tile (at most), threads per block, tiles, and the SpMV variant (8, 16,
+ * 32: segmented with that many nonzeros per thread; -4, -8: vector with that
+ * many lanes per row).  Any pointer may be NULL.  */
 pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int32_t* a_block,
                               int32_t* a_tiles, int32_t* at_tile_nnz, int32_t* at_block,
-                              int32_t* at_tiles);
+                              int32_t* at_tiles, int32_t* a_variant, int32_t* at_variant);
 
 /* ---- batched solves -------------------------------------------------------
  * `count` independent LPs iterated together as one block-diagonal system: each

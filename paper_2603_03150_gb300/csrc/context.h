@@ -47,8 +47,9 @@ struct HostSched {
 // longer row, or runs of empty rows.
 // With lp_off (count + 1 row offsets) no tile crosses an LP boundary and each
 // tile records its LP.
+// cap > 0: at most cap nonzeros per tile (below the full capacity).
 HostSched build_sched(const int32_t* rp, int nrows, int e, const int64_t* lp_off = nullptr,
-                      int count = 1);
+                      int count = 1, int cap = 0);
 
 struct DevSched {
   Tile* tiles = nullptr;

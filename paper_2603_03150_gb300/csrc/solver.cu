@@ -50,10 +50,13 @@ namespace pdhg {
 // Tiles: runs of whole rows with at most tile_capacity(kBlock, e) nonzeros
 // and at most tile_max_rows(kBlock) rows; a longer row becomes a split group
 // of capacity-sized chunks.
-HostSched build_sched(const int32_t* rp, int nrows, int e, const int64_t* lp_off, int count) {
+HostSched build_sched(const int32_t* rp, int nrows, int e, const int64_t* lp_off, int count,
+                      int cap) {
   HostSched h;
-  // vector schedules (e < 0) use the tile capacity of e = 8
-  const int cap = tile_capacity(kBlock, e > 0 ? e : 8);
+  // vector schedules (e < 0) use the tile capacity of e = 8; a smaller
+  // capacity leaves the last thread windows of a full tile empty
+  const int full = tile_capacity(kBlock, e > 0 ? e : 8);
+  cap = (cap > 0 && cap < full) ? cap : full;
   h.tile_nnz = cap;
   h.max_rows = tile_max_rows(kBlock);
   h.e = e;
@@ -354,25 +357,27 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
     const int nrows = on_a ? ctx->m : ctx->n;
     int64_t longest = 0;
     for (int r = 0; r < nrows; ++r) longest = std::max<int64_t>(longest, rp[r + 1] - rp[r]);
-    std::vector<int> cands;
-    if (ctx->opt.tile_nnz < 0)  // forced vector variant (only where rows are short)
-      cands.push_back(longest <= 256 ? (ctx->opt.tile_nnz <= -8 ? -8 : -4) : 8);
-    else if (ctx->opt.tile_nnz > 0)
-      cands.push_back(ctx->opt.tile_nnz <= 2048 ? 8 : (ctx->opt.tile_nnz <= 4096 ? 16 : 32));
+    std::vector<std::pair<int, int>> cands;  // (variant, tile capacity; 0 = full)
+    const int tn = ctx->opt.tile_nnz;
+    if (tn < 0)  // forced vector variant (only where rows are short)
+      cands.push_back({longest <= 256 ? (tn <= -8 ? -8 : -4) : 8, 0});
+    else if (tn > 0)
+      cands.push_back({tn <= 2044 ? 8 : (tn <= 4092 ? 16 : 32), tn});
     else if (ctx->opt.autotune) {
-      cands = {8, 16, 32};
-      if (longest <= 256) cands.insert(cands.end(), {-4, -8});
+      cands = {{8, 0}, {16, 0}, {32, 0}};
+      if (longest <= 256) cands.insert(cands.end(), {{-4, 0}, {-8, 0}});
     } else {
-      cands = {8};
+      cands = {{8, 0}};
     }
     DevSched best{};
     float best_ms = 1e30f;
-    for (int e : cands) {
+    for (const auto& cand : cands) {
+      const int e = cand.first;
       DevSched d;
-      if (e == kFixedE) {
+      if (e == kFixedE && cand.second == 0) {
         d = on_a ? ctx->sa8 : ctx->st8;
       } else {
-        HostSched h = build_sched(rp.data(), nrows, e);
+        HostSched h = build_sched(rp.data(), nrows, e, nullptr, 1, cand.second);
         CKS(upload_sched(ctx, h, &d, on_a ? ctx->a_rp : ctx->t_rp));
       }
       (on_a ? ctx->sa : ctx->st) = d;
@@ -1218,7 +1223,8 @@ extern "C" pdhg_status pdhg_get_kernel_timing(pdhg_ctx* ctx, double* primal_ms, 
 
 extern "C" pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int32_t* a_block,
                                          int32_t* a_tiles, int32_t* at_tile_nnz,
-                                         int32_t* at_block, int32_t* at_tiles) {
+                                         int32_t* at_block, int32_t* at_tiles,
+                                         int32_t* a_variant, int32_t* at_variant) {
   g_last_error.clear();
   if (!ctx) {
     set_error("ctx is NULL");
@@ -1230,6 +1236,8 @@ extern "C" pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int
   if (at_tile_nnz) *at_tile_nnz = ctx->st.view.tile_nnz;
   if (at_block) *at_block = kBlock;
   if (at_tiles) *at_tiles = ctx->st.view.ntiles;
+  if (a_variant) *a_variant = ctx->sa.view.e;
+  if (at_variant) *at_variant = ctx->st.view.e;
   return PDHG_OK;
 }
 

@@ -81,7 +81,7 @@ _SIGS = {
     "pdhg_set_state": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "pdhg_get_log": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "pdhg_get_kernel_timing": (_I32, [_P, _P, _P, _P]),
-    "pdhg_get_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+    "pdhg_get_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pdhg_get_launch_count": (_I32, [_P, _P]),
     "pdhg_batch_create": (_I32, [_PP, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
     "pdhg_batch_solve": (_I32, [_P, _D, _I64, _P]),
@@ -302,9 +302,10 @@ class Solver:
         return dict(primal_ms=a.value, dual_ms=d.value, samples=s.value)
 
     def schedule(self):
-        v = [_I32() for _ in range(6)]
+        v = [_I32() for _ in range(8)]
         _check(self._L.pdhg_get_schedule(self._ctx, *[ctypes.byref(x) for x in v]))
-        keys = ["a_tile_nnz", "a_block", "a_tiles", "at_tile_nnz", "at_block", "at_tiles"]
+        keys = ["a_tile_nnz", "a_block", "a_tiles", "at_tile_nnz", "at_block", "at_tiles",
+                "a_variant", "at_variant"]
         return {k: x.value for k, x in zip(keys, v)}
 
     def launch_count(self) -> int:

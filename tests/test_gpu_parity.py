@@ -65,6 +65,36 @@ def heavy_row_lp(seed=0):
     return lpgen.powerlaw_lp(m=3000, n=12000, nnz=90000, k_max=9000, seed=seed)
 
 
+def gappy_lp(seed=0):
+    """Runs of empty rows and empty columns (1200 / 1500 in a row: longer than
+    a tile's row limit), rows and columns longer than any tile (split rows in
+    A and A^T), single-entry rows, and a planted optimum."""
+    rng = np.random.default_rng(seed)
+    m, n = 4500, 6000
+    live_r = np.r_[0:100, 1300:m]
+    live_c = np.r_[0:2000, 3500:n]
+    rows, cols = [], []
+    for j in live_c:  # ~3 entries per live column
+        k = int(rng.integers(1, 6))
+        rows.append(rng.choice(live_r, size=k, replace=False))
+        cols.append(np.full(k, j))
+    rows.append(np.full(4500, 1500))  # a row of 4500 entries
+    cols.append(rng.choice(live_c, size=4500, replace=False))
+    rows.append(rng.choice(live_r, size=2500, replace=False))  # a column of 2500 entries
+    cols.append(np.full(2500, 10))
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    A = sp.coo_matrix((rng.standard_normal(rows.size), (rows, cols)), shape=(m, n)).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    x = rng.uniform(0.5, 2, n) * (rng.random(n) < 0.3)
+    y = rng.standard_normal(m)
+    z = np.where(x > 0, 0.0, rng.uniform(0.5, 2, n))
+    b = A @ x
+    c = A.T @ y + z
+    return lpgen.LP(m, n, A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.copy(), b, c,
+                    x, y, z, name="gappy")
+
+
 # ----------------------------------------------------------------- a1
 @pytest.mark.parametrize("maker", [lambda: lpgen.planted_lp(200, 500, seed=0), dense_column_lp,
                                    heavy_row_lp])
@@ -104,9 +134,12 @@ def _compare_state(st, ost, tol):
     assert abs(st["omega"] - ost.omega) <= tol * ost.omega
 
 
-@pytest.mark.parametrize("tile_nnz", [0, 512, 4096, -4, -8])
+# tile_nnz: autotuned; 8 nonzeros per thread at reduced capacities (100: most
+# rows split); 16 per thread (3000); 32 per thread, 64-bit window words (8000);
+# the vector variant (falls back to segmented where rows exceed 256)
+@pytest.mark.parametrize("tile_nnz", [0, 100, 512, 1371, 3000, 8000, -4, -8])
 @pytest.mark.parametrize("maker", [lambda: lpgen.planted_lp(200, 500, seed=0), heavy_row_lp,
-                                   dense_column_lp])
+                                   dense_column_lp, gappy_lp])
 def test_fp64_iterates_after_100(maker, tile_nnz):
     lp = maker()
     r = O.solve(lp, 1e-12, 100)
