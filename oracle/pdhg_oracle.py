@@ -44,6 +44,21 @@ CUDA path implements independently:
   primal-weight update with theta = 0.5.
 These constants are a convention shared with the CUDA path: parity unpinned
 against the paper for the restart constants, the omega rule and eta.
+
+Optional iteration (``Options.method = "halpern"``): the reflected Halpern
+scheme of cuPDLP+, the solver Section 4.1 says its PDHG follows (the paper
+prints none of its formulas; this is the reading).  With T the PDHG map
+above, z = (x, y), anchor z0 = the last restart point and t the iterations
+since it,
+      z_{t+1} = lam_t ((1 + rho) T(z_t) - rho z_t) + (1 - lam_t) z0,
+      lam_t = (t + 1) / (t + 2),  rho = Options.reflection in [0, 1];
+the second candidate of the evaluation (where the averaged method uses the
+running average) is T(z_t), the last PDHG output; evaluation, termination,
+restart rule and omega update are unchanged.  Pinned by the Halpern bound
+||z_t - T z_t||_M <= 2 ||z_0 - z*||_M / ((1 + rho)(t + 1)) for the PDHG
+metric M (T is firmly nonexpansive in M, so (1+rho)T - rho I is
+nonexpansive for rho <= 1), and by the rho = 1 first step being one plain
+PDHG step.
 """
 from __future__ import annotations
 
@@ -70,6 +85,8 @@ class Options:
     beta_artificial: float = 0.36
     theta: float = 0.5
     omega_update_min: float = 1e-10
+    method: str = "averaged"   # or "halpern" (reflected Halpern, see the header)
+    reflection: float = 1.0    # rho of the Halpern method, in [0, 1]
 
 
 # ---------------------------------------------------------------------------
@@ -312,7 +329,8 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
     """Restarted PDHG until the Section 2 test holds or max_iter iterations.
 
     Evaluation points are k % F == 0 and k == max_iter.  At each: the
-    termination test on the current iterate, then on the average; at
+    termination test on the current iterate, then on the average (Halpern
+    method: on T of the previous iterate); at
     k == max_iter the loop stops; otherwise (k % F == 0) the restart rule:
     candidate = the lower KKT error (tie: current); restart if
       (i)   KKT(cand) <= beta_suff * KKT(last restart), or
@@ -330,13 +348,26 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
     status, chosen = STATUS_MAX_ITER, "current"
     xs_out, ys_out = st.x, st.y
 
+    halpern = opts.method == "halpern"
+    if opts.method not in ("averaged", "halpern") or not 0.0 <= opts.reflection <= 1.0:
+        raise ValueError("method must be 'averaged' or 'halpern', reflection in [0, 1]")
     while st.k < max_iter:
         tau, sigma = S.eta / st.omega, S.eta * st.omega
-        st.x, st.y = pdhg_step(At, b_t, c_t, st.x, st.y, tau, sigma)
-        st.k += 1
-        st.t += 1
-        st.x_avg = st.x_avg + (st.x - st.x_avg) / st.t
-        st.y_avg = st.y_avg + (st.y - st.y_avg) / st.t
+        if halpern:
+            # z <- lam ((1 + rho) T(z) - rho z) + (1 - lam) z0, z0 = last restart point
+            xh, yh = pdhg_step(At, b_t, c_t, st.x, st.y, tau, sigma)
+            lam, rho = (st.t + 1.0) / (st.t + 2.0), opts.reflection
+            st.x = lam * ((1.0 + rho) * xh - rho * st.x) + (1.0 - lam) * st.x_last
+            st.y = lam * ((1.0 + rho) * yh - rho * st.y) + (1.0 - lam) * st.y_last
+            st.x_avg, st.y_avg = xh, yh  # second candidate: T(z)
+            st.k += 1
+            st.t += 1
+        else:
+            st.x, st.y = pdhg_step(At, b_t, c_t, st.x, st.y, tau, sigma)
+            st.k += 1
+            st.t += 1
+            st.x_avg = st.x_avg + (st.x - st.x_avg) / st.t
+            st.y_avg = st.y_avg + (st.y - st.y_avg) / st.t
         if st.k % F != 0 and st.k != max_iter:
             continue
         # termination, current iterate first (Section 2 inequalities)

@@ -272,3 +272,102 @@ def test_running_average_is_mean_of_iterates():
     np.testing.assert_allclose(r.state.x, x, rtol=0, atol=1e-14)
     np.testing.assert_allclose(r.state.x_avg, np.mean(xs, axis=0), rtol=0, atol=1e-12)
     np.testing.assert_allclose(r.state.y_avg, np.mean(ys, axis=0), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------ reflected Halpern (optional)
+def _m_norm2(A, tau, sigma, x, y):
+    """||(x, y)||_M^2 for the PDHG metric M = [[I/tau, A^T], [A, I/sigma]] of
+    the update x+ = P(x - tau(c - A^T y)), y+ = y + sigma(b - A(2x+ - x))
+    (A is the scaled m x n matrix)."""
+    return float(x @ x / tau + y @ y / sigma + 2.0 * (y @ (A @ x)))
+
+
+def _m_inner(A, tau, sigma, u, v):
+    (ux, uy), (vx, vy) = u, v
+    return float(ux @ vx / tau + uy @ vy / sigma + uy @ (A @ vx) + vy @ (A @ ux))
+
+
+def test_pdhg_step_is_firmly_nonexpansive_in_the_pdhg_metric():
+    """The PDHG map is the resolvent of a monotone operator in the metric M:
+    ||Tz - Tw||_M^2 <= <Tz - Tw, z - w>_M for any z, w.  A sign slip in the
+    extrapolation or a transposed product breaks it for some pair."""
+    lp = lpgen.planted_lp(40, 90, seed=3)
+    S = O.setup(lp)
+    At, b_t, c_t = S.At, S.b_t, S.c_t
+    m, n = At.shape
+    tau, sigma = S.eta / S.omega0, S.eta * S.omega0
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        z = (rng.standard_normal(n), rng.standard_normal(m))
+        w = (rng.standard_normal(n), rng.standard_normal(m))
+        Tz = O.pdhg_step(At, b_t, c_t, *z, tau, sigma)
+        Tw = O.pdhg_step(At, b_t, c_t, *w, tau, sigma)
+        d = (Tz[0] - Tw[0], Tz[1] - Tw[1])
+        lhs = _m_norm2(At, tau, sigma, *d)
+        rhs = _m_inner(At, tau, sigma, d, (z[0] - w[0], z[1] - w[1]))
+        assert lhs <= rhs * (1 + 1e-12) + 1e-12
+
+
+def test_halpern_first_step_with_full_reflection_is_one_pdhg_step():
+    """rho = 1, t = 0: lam = 1/2 and z1 = (2 T(z0) - z0)/2 + z0/2 = T(z0)."""
+    lp = lpgen.planted_lp(30, 70, seed=1)
+    ra = O.solve(lp, 1e-15, 1)
+    rh = O.solve(lp, 1e-15, 1, opts=O.Options(method="halpern", reflection=1.0))
+    np.testing.assert_allclose(rh.state.x, ra.state.x, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(rh.state.y, ra.state.y, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("start", ["zero", "restart_point"])
+@pytest.mark.parametrize("rho", [0.0, 0.5, 1.0])
+def test_halpern_fixed_point_residual_bound(rho, start):
+    """Without restarts, Halpern's iteration on the nonexpansive operator
+    R = (1 + rho) T - rho I with lam_t = (t+1)/(t+2) satisfies
+    ||z_t - R z_t||_M <= 2 ||z_0 - z*||_M / (t + 1); since z - Rz = (1+rho)(z - Tz)
+    this is ||z_t - T z_t||_M <= 2 ||z_0 - z*||_M / ((1 + rho)(t + 1)) for every
+    saddle point z* (here the planted one, scaled).  A wrong weight, a missing
+    anchor term or a wrong reflection breaks it within the first iterations."""
+    lp = lpgen.planted_lp(60, 150, seed=2)
+    opts = O.Options(method="halpern", reflection=rho, beta_sufficient=0.0,
+                     beta_necessary=0.0, beta_artificial=1e30)
+    S = O.setup(lp, opts)
+    At, b_t, c_t = S.At, S.b_t, S.c_t
+    tau, sigma = S.eta / S.omega0, S.eta * S.omega0
+    xs, ys = lp.x_star / S.D_c, lp.y_star / S.D_r
+    # z* is a fixed point of T (the planted pair is a saddle point)
+    Tx, Ty = O.pdhg_step(At, b_t, c_t, xs, ys, tau, sigma)
+    assert np.max(np.abs(Tx - xs)) < 1e-9 and np.max(np.abs(Ty - ys)) < 1e-9
+    st = O.initial_state(S)
+    if start == "restart_point":  # as right after a restart: z = z0 = anchor != 0
+        rng = np.random.default_rng(5)
+        st.x = st.x_last = rng.uniform(0.0, 2.0, st.x.size)
+        st.y = st.y_last = rng.standard_normal(st.y.size)
+    r0 = np.sqrt(_m_norm2(At, tau, sigma, st.x - xs, st.y - ys))
+    for t in range(1, 201):
+        res = O.solve(lp, 1e-300, t, opts=opts, S=S, state=st)
+        st = res.state
+        assert st.restarts == 0 and st.t == t
+        Tx, Ty = O.pdhg_step(At, b_t, c_t, st.x, st.y, tau, sigma)
+        g = np.sqrt(max(0.0, _m_norm2(At, tau, sigma, st.x - Tx, st.y - Ty)))
+        assert g <= 2.0 * r0 / ((1.0 + rho) * (t + 1)) * (1 + 1e-9), t
+
+
+def test_halpern_solve_reaches_the_planted_optimum():
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    r = O.solve(lp, 1e-8, 200_000, opts=O.Options(method="halpern"))
+    assert r.status == O.STATUS_CONVERGED
+    opt = float(lp.c @ lp.x_star)
+    assert abs(float(lp.c @ r.x) - opt) <= 1e-6 * (1 + abs(opt))
+    assert np.max(np.abs(r.x - lp.x_star)) < 1e-5
+
+
+def test_halpern_second_candidate_is_the_projected_pdhg_output():
+    """The reflected iterate leaves the cone x >= 0 (2 x^ - x < 0 where x^ = 0 <
+    x), the PDHG output T(z) never does: the evaluation's second candidate
+    (and any iterate returned as 'average') is T(z), not z."""
+    lp = lpgen.planted_lp(200, 500, seed=4)
+    r = O.solve(lp, 1e-300, 100, opts=O.Options(method="halpern", reflection=1.0))
+    assert np.min(r.state.x) < 0.0           # the iterate itself is outside
+    assert np.min(r.state.x_avg) >= 0.0      # the candidate is inside
+    r2 = O.solve(lp, 1e-4, 200_000, opts=O.Options(method="halpern", reflection=1.0))
+    if r2.chosen == "average":
+        assert np.min(r2.x_scaled) >= 0.0
