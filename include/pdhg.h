@@ -81,6 +81,14 @@ typedef struct pdhg_options {
   int32_t kernel_timing;   /* 1: sample primal/dual kernel durations with CUDA
                               events during pdhg_solve                          */
   int32_t verbose;
+  int32_t method;          /* 0 (default): restarted averaged PDHG; 1: reflected
+                              Halpern iteration of cuPDLP+, the solver Section
+                              4.1 says its PDHG follows: z <- lam((1 + rho) T(z)
+                              - rho z) + (1 - lam) z0, lam = (t+1)/(t+2), z0 =
+                              the last restart point, T = one PDHG step; the
+                              evaluation's second candidate is T(z) (single-LP
+                              contexts only)                                   */
+  double reflection;       /* rho of method 1, in [0, 1] (default 1)           */
 } pdhg_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -13,6 +13,7 @@
 #include <cstring>
 
 #include "context.h"
+#include "dispatch.cuh"
 #include "eval_rule.cuh"
 
 namespace pdhg {
@@ -672,38 +673,6 @@ __global__ void k_bglobalize(const int64_t* nnz_off, const int64_t* n_off, int32
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-#define PDHG_BDISPATCH_E(e, ...)   \
-  switch (e) {                     \
-    case -4: {                     \
-      constexpr int E_ = -4;       \
-      __VA_ARGS__;                 \
-    } break;                       \
-    case -8: {                     \
-      constexpr int E_ = -8;       \
-      __VA_ARGS__;                 \
-    } break;                       \
-    case 32: {                     \
-      constexpr int E_ = 32;       \
-      __VA_ARGS__;                 \
-    } break;                       \
-    case 16: {                     \
-      constexpr int E_ = 16;       \
-      __VA_ARGS__;                 \
-    } break;                       \
-    default: {                     \
-      constexpr int E_ = 8;        \
-      __VA_ARGS__;                 \
-    } break;                       \
-  }
-
-static cudaError_t set_dyn(const void* f, size_t max_smem) {
-  cudaFuncAttributes a;
-  cudaError_t r = cudaFuncGetAttributes(&a, f);
-  if (r == cudaSuccess)
-    r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(max_smem - a.sharedSizeBytes));
-  return r;
-}
 
 template <int E>
 static cudaError_t configure_batch_e(size_t mx) {
@@ -712,7 +681,7 @@ static cudaError_t configure_batch_e(size_t mx) {
        {(const void*)k_bprimal<float, kBlock, E>, (const void*)k_bprimal<double, kBlock, E>,
         (const void*)k_bdual<float, kBlock, E>, (const void*)k_bdual<double, kBlock, E>,
         (const void*)k_beval<float, kBlock, E>, (const void*)k_beval<double, kBlock, E>}) {
-    cudaError_t r = set_dyn(f, mx);
+    cudaError_t r = set_max_dyn_smem(f, mx);
     if (r != cudaSuccess) e = r;
   }
   return e;
@@ -727,7 +696,7 @@ static cudaError_t configure_batch_kernels(size_t mx) {
   for (const void* f : {(const void*)k_bpow_Av<kBlock>, (const void*)k_bpow_ATu<kBlock>,
                         (const void*)k_brep_n<kBlock>, (const void*)k_brep_m<kBlock>,
                         (const void*)k_bws_z<kBlock>}) {
-    cudaError_t r = set_dyn(f, mx);
+    cudaError_t r = set_max_dyn_smem(f, mx);
     if (r != cudaSuccess) e = r;
   }
   return e;
@@ -762,6 +731,7 @@ static BatchBuffers<T> batch_buffers(pdhg_ctx* ctx) {
   I.y_last = (T*)ctx->y_last;
   I.Ax = (T*)ctx->Ax;
   I.Ax_avg = (T*)ctx->Ax_avg;
+  I.Ax_last = (T*)ctx->Ax_last;
   I.c_t64 = ctx->c_t64;
   I.b_t64 = ctx->b_t64;
   I.D_r = ctx->D_r;
@@ -783,14 +753,14 @@ static void enqueue_bchunk(pdhg_ctx* ctx, int len) {
   const BatchBuffers<T> B = batch_buffers<T>(ctx);
   ctx->launches += 2LL * len + 2;
   for (int i = 0; i < len; ++i) {
-    PDHG_BDISPATCH_E(B.it.t_sched.e,
+    PDHG_DISPATCH_E(B.it.t_sched.e,
                      (k_bprimal<T, kBlock, E_><<<ctx->l_prim.grid, kBlock, ctx->l_prim.smem,
                                                   ctx->stream>>>(B, i)));
-    PDHG_BDISPATCH_E(B.it.a_sched.e,
+    PDHG_DISPATCH_E(B.it.a_sched.e,
                      (k_bdual<T, kBlock, E_><<<ctx->l_dual.grid, kBlock, ctx->l_dual.smem,
                                                 ctx->stream>>>(B, i)));
   }
-  PDHG_BDISPATCH_E(B.it.t_sched.e,
+  PDHG_DISPATCH_E(B.it.t_sched.e,
                    (k_beval<T, kBlock, E_><<<ctx->l_eval.grid, kBlock, ctx->l_eval.smem,
                                               ctx->stream>>>(B, len)));
   k_brestart<T><<<ctx->restart_grid, 256, 0, ctx->stream>>>(B);
@@ -838,11 +808,11 @@ static pdhg_status time_batch_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out) {
   for (int it = 0; it < warm + reps; ++it) {
     if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
     if (on_a) {
-      PDHG_BDISPATCH_E(B.it.a_sched.e,
+      PDHG_DISPATCH_E(B.it.a_sched.e,
                        (k_bdual<T, kBlock, E_><<<ctx->l_dual.grid, kBlock, ctx->l_dual.smem,
                                                   ctx->stream>>>(B, 0)));
     } else {
-      PDHG_BDISPATCH_E(B.it.t_sched.e,
+      PDHG_DISPATCH_E(B.it.t_sched.e,
                        (k_bprimal<T, kBlock, E_><<<ctx->l_prim.grid, kBlock, ctx->l_prim.smem,
                                                     ctx->stream>>>(B, 0)));
     }
@@ -929,7 +899,7 @@ static pdhg_status tune_batch_schedules(pdhg_ctx* ctx) {
   const size_t es = elem(ctx);
   for (void* p : {ctx->x, ctx->x_avg, ctx->x_last})
     CK(cudaMemsetAsync(p, 0, es * ctx->n, ctx->stream));
-  for (void* p : {ctx->y, ctx->y_avg, ctx->y_last, ctx->Ax, ctx->Ax_avg})
+  for (void* p : {ctx->y, ctx->y_avg, ctx->y_last, ctx->Ax, ctx->Ax_avg, ctx->Ax_last})
     CK(cudaMemsetAsync(p, 0, es * ctx->m, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return PDHG_OK;
@@ -1122,8 +1092,10 @@ extern "C" pdhg_status pdhg_batch_create(pdhg_ctx** out, int32_t count, const in
   else
     pdhg_default_options(&ctx->opt);
   if (ctx->opt.eval_freq < 1 ||
-      (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED)) {
-    set_error("invalid options (eval_freq >= 1, precision 0/1)");
+      (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED) ||
+      ctx->opt.method != 0) {
+    set_error("invalid options (eval_freq >= 1, precision 0/1, method 0: batched solves use "
+              "the averaged iteration)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }

@@ -91,7 +91,7 @@ struct pdhg_ctx {
          *D_c = nullptr;
   float *b_t32 = nullptr, *c_t32 = nullptr;
   void *x = nullptr, *y = nullptr, *x_avg = nullptr, *y_avg = nullptr, *x_last = nullptr,
-       *y_last = nullptr, *Ax = nullptr, *Ax_avg = nullptr;
+       *y_last = nullptr, *Ax = nullptr, *Ax_avg = nullptr, *Ax_last = nullptr;
   double *xs64 = nullptr, *ys64 = nullptr, *out_n1 = nullptr, *out_n2 = nullptr,
          *out_m1 = nullptr, *report = nullptr, *sums = nullptr;
   Scalars* sc = nullptr;

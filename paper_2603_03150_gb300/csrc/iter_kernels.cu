@@ -4,6 +4,7 @@
 // an iterate, and Algorithm 1 (centered start point, Section 3.1).
 #include <math.h>
 
+#include "dispatch.cuh"
 #include "eval_rule.cuh"
 #include "kernels.h"
 #include "spmv_tile.cuh"
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
   }
 }
 
-// Restart: the candidate becomes the iterate and the new last restart point.
+// Restart: the candidate becomes the iterate and the new last restart point
+// (with its product A~x, the Halpern method's anchor term).
 template <typename T>
 __global__ void k_restart(IterBuffers<T> B) {
   if (!B.sc->restart_pending) return;
@@ -202,39 +204,17 @@ __global__ void k_restart(IterBuffers<T> B) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.m; i += stride) {
     if (avg) {
       const T v = B.y_avg[i];
+      const T h = B.Ax_avg[i];
       B.y[i] = v;
       B.y_last[i] = v;
-      B.Ax[i] = B.Ax_avg[i];
+      B.Ax[i] = h;
+      B.Ax_last[i] = h;
     } else {
       B.y_last[i] = B.y[i];
+      B.Ax_last[i] = B.Ax[i];
     }
   }
 }
-
-// nonzeros per thread of a schedule -> template instantiation
-#define PDHG_DISPATCH_E(e, ...)                 \
-  switch (e) {                                  \
-    case -4: {                                  \
-      constexpr int E_ = -4;                    \
-      __VA_ARGS__;                              \
-    } break;                                    \
-    case -8: {                                  \
-      constexpr int E_ = -8;                    \
-      __VA_ARGS__;                              \
-    } break;                                    \
-    case 32: {                                  \
-      constexpr int E_ = 32;                    \
-      __VA_ARGS__;                              \
-    } break;                                    \
-    case 16: {                                  \
-      constexpr int E_ = 16;                    \
-      __VA_ARGS__;                              \
-    } break;                                    \
-    default: {                                  \
-      constexpr int E_ = 8;                     \
-      __VA_ARGS__;                              \
-    } break;                                    \
-  }
 
 template <typename T>
 void launch_primal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s) {
@@ -570,14 +550,6 @@ size_t tile_smem(int nv, bool f32, int max_rows, int e) {
   return f32 ? tile_smem_bytes<float, 2, kBlock>(max_rows) : tile_smem_bytes<double, 2, kBlock>(max_rows);
 }
 
-static cudaError_t set_max_dyn(const void* f, size_t max_smem) {
-  cudaFuncAttributes a;
-  cudaError_t r = cudaFuncGetAttributes(&a, f);
-  if (r == cudaSuccess)
-    r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(max_smem - a.sharedSizeBytes));
-  return r;
-}
 
 template <int E>
 static const void* tile_kernel(int which) {
@@ -608,11 +580,11 @@ cudaError_t configure_tile_kernels(size_t max_smem) {
   for (int w = 0; w < 8; ++w)
     for (const void* f : {tile_kernel<8>(w), tile_kernel<16>(w), tile_kernel<32>(w),
                           tile_kernel<-4>(w), tile_kernel<-8>(w)}) {
-      cudaError_t r = set_max_dyn(f, max_smem);
+      cudaError_t r = set_max_dyn_smem(f, max_smem);
       if (r != cudaSuccess) e = r;
     }
   for (int w = 0; w < 3; ++w) {
-    cudaError_t r = set_max_dyn(fixed_kernel(w), max_smem);
+    cudaError_t r = set_max_dyn_smem(fixed_kernel(w), max_smem);
     if (r != cudaSuccess) e = r;
   }
   return e;

@@ -20,7 +20,11 @@ struct IterBuffers {
   const int32_t *t_rp, *t_col;  // A~^T (rows = n)
   const T* t_val;
   SchedView a_sched, t_sched;
-  T *x, *y, *x_avg, *y_avg, *x_last, *y_last, *Ax, *Ax_avg;
+  // averaged method: x_avg, y_avg, Ax_avg are the running averages;
+  // Halpern method: they hold T(z) = (x^, y^) and A~x^, and x_last, y_last,
+  // Ax_last the anchor (last restart point) and its product
+  T *x, *y, *x_avg, *y_avg, *x_last, *y_last, *Ax, *Ax_avg, *Ax_last;
+  double rho;  // Halpern reflection
   const T *c_t, *b_t;                       // scaled c, b in precision T
   const double *c_t64, *b_t64, *D_r, *D_c;  // float64 copies and scalings
   Scalars* sc;
@@ -134,6 +138,15 @@ void launch_init_scalars(Scalars* sc, const double* sums, const PowerState* ps,
 cudaError_t configure_setup_kernels(size_t max_smem);
 cudaError_t configure_tile_kernels(size_t max_smem);
 int tile_occupancy(int which, int e, size_t smem);
+
+// ---- reflected Halpern half-steps (halpern.cu) ----------------------------
+template <typename T>
+void launch_hprimal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
+template <typename T>
+void launch_hdual(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
+cudaError_t configure_halpern_kernels(size_t max_smem);
+// blocks per SM (which: 0/1 primal f32/f64, 2/3 dual f32/f64)
+int halpern_occupancy(int which, int e, size_t smem);
 size_t tile_smem(int nv, bool f32, int max_rows, int e);
 
 }  // namespace pdhg

@@ -176,8 +176,19 @@ pdhg_status pdhg::upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d,
   return PDHG_OK;
 }
 
+// occupancy kinds of the iteration kernels (tile_occupancy numbering; the
+// Halpern kernels from kOccHalpern on)
+static constexpr int kOccHalpern = 100;
+static int prim_kind(const pdhg_ctx* ctx) {
+  return (ctx->opt.method == 1 ? kOccHalpern : 0) + (ctx->mixed ? 0 : 1);
+}
+static int dual_kind(const pdhg_ctx* ctx) {
+  return (ctx->opt.method == 1 ? kOccHalpern : 0) + (ctx->mixed ? 2 : 3);
+}
+
 Launch pdhg::make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int ntiles) {
-  const int occ = tile_occupancy(occ_kind, e, smem);
+  const int occ = occ_kind >= kOccHalpern ? halpern_occupancy(occ_kind - kOccHalpern, e, smem)
+                                          : tile_occupancy(occ_kind, e, smem);
   int grid = std::min(ntiles, ctx->nsm * occ);
   return Launch{std::max(grid, 1), smem};
 }
@@ -274,6 +285,8 @@ static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
   B.y_last = (T*)ctx->y_last;
   B.Ax = (T*)ctx->Ax;
   B.Ax_avg = (T*)ctx->Ax_avg;
+  B.Ax_last = (T*)ctx->Ax_last;
+  B.rho = ctx->opt.reflection;
   B.c_t64 = ctx->c_t64;
   B.b_t64 = ctx->b_t64;
   B.D_r = ctx->D_r;
@@ -289,6 +302,22 @@ static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
   return B;
 }
 
+// the iteration's half-steps for the configured method
+template <typename T>
+static void launch_prim_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i) {
+  if (ctx->opt.method == 1)
+    launch_hprimal<T>(B, ctx->l_prim, i, ctx->stream);
+  else
+    launch_primal<T>(B, ctx->l_prim, i, ctx->stream);
+}
+template <typename T>
+static void launch_dual_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i) {
+  if (ctx->opt.method == 1)
+    launch_hdual<T>(B, ctx->l_dual, i, ctx->stream);
+  else
+    launch_dual<T>(B, ctx->l_dual, i, ctx->stream);
+}
+
 // `len` iterations followed by the evaluation and the restart.  With
 // `timing`, events bracket the primal and dual kernels of iteration len/2.
 template <typename T>
@@ -298,12 +327,12 @@ static void enqueue_chunk(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
   for (int i = 0; i < len; ++i) {
     const bool sample = timing && i == len / 2;
     if (sample) cudaEventRecordWithFlags(timing[0], ctx->stream, cudaEventRecordExternal);
-    launch_primal<T>(B, ctx->l_prim, i, ctx->stream);
+    launch_prim_step<T>(ctx, B, i);
     if (sample) {
       cudaEventRecordWithFlags(timing[1], ctx->stream, cudaEventRecordExternal);
       cudaEventRecordWithFlags(timing[2], ctx->stream, cudaEventRecordExternal);
     }
-    launch_dual<T>(B, ctx->l_dual, i, ctx->stream);
+    launch_dual_step<T>(ctx, B, i);
     if (sample) cudaEventRecordWithFlags(timing[3], ctx->stream, cudaEventRecordExternal);
   }
   launch_eval<T>(B, ctx->l_eval, len, ctx->stream);
@@ -334,9 +363,9 @@ static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out
   for (int it = 0; it < warm + reps; ++it) {
     if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
     if (on_a)
-      launch_dual<T>(B, ctx->l_dual, 0, ctx->stream);
+      launch_dual_step<T>(ctx, B, 0);
     else
-      launch_primal<T>(B, ctx->l_prim, 0, ctx->stream);
+      launch_prim_step<T>(ctx, B, 0);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(e1, ctx->stream));
@@ -382,10 +411,10 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
       }
       (on_a ? ctx->sa : ctx->st) = d;
       if (on_a)
-        ctx->l_dual = make_launch(ctx, mx ? 2 : 3, d.view.e,
+        ctx->l_dual = make_launch(ctx, dual_kind(ctx), d.view.e,
                                   smem_for(0, mx, d.view.max_rows, d.view.e), d.view.ntiles);
       else
-        ctx->l_prim = make_launch(ctx, mx ? 0 : 1, d.view.e,
+        ctx->l_prim = make_launch(ctx, prim_kind(ctx), d.view.e,
                                   smem_for(0, mx, d.view.max_rows, d.view.e), d.view.ntiles);
       float ms = 0.f;
       if (cands.size() > 1) {
@@ -403,8 +432,8 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
     (on_a ? ctx->sa : ctx->st) = best;
   }
   const SchedView &A = ctx->sa.view, &T = ctx->st.view;
-  ctx->l_prim = make_launch(ctx, mx ? 0 : 1, T.e, smem_for(0, mx, T.max_rows, T.e), T.ntiles);
-  ctx->l_dual = make_launch(ctx, mx ? 2 : 3, A.e, smem_for(0, mx, A.max_rows, A.e), A.ntiles);
+  ctx->l_prim = make_launch(ctx, prim_kind(ctx), T.e, smem_for(0, mx, T.max_rows, T.e), T.ntiles);
+  ctx->l_dual = make_launch(ctx, dual_kind(ctx), A.e, smem_for(0, mx, A.max_rows, A.e), A.ntiles);
   {
     const size_t sm = smem_for(1, mx, T.max_rows, T.e);
     const int occ = tile_occupancy(mx ? 4 : 5, T.e, sm);
@@ -417,7 +446,7 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
   const size_t es = elem(ctx);
   for (void* p : {ctx->x, ctx->x_avg, ctx->x_last})
     CK(cudaMemsetAsync(p, 0, es * ctx->n, ctx->stream));
-  for (void* p : {ctx->y, ctx->y_avg, ctx->y_last, ctx->Ax, ctx->Ax_avg})
+  for (void* p : {ctx->y, ctx->y_avg, ctx->y_last, ctx->Ax, ctx->Ax_avg, ctx->Ax_last})
     CK(cudaMemsetAsync(p, 0, es * ctx->m, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return PDHG_OK;
@@ -469,6 +498,8 @@ extern "C" void pdhg_default_options(pdhg_options* o) {
   o->tile_nnz = 0;
   o->kernel_timing = 0;
   o->verbose = 0;
+  o->method = 0;
+  o->reflection = 1.0;
 }
 
 // device attributes, stream, kernel shared-memory limits
@@ -486,6 +517,7 @@ pdhg_status pdhg::setup_device(pdhg_ctx* ctx) {
     ctx->own_stream = true;
   }
   CK(configure_tile_kernels(ctx->smem_optin));
+  CK(configure_halpern_kernels(ctx->smem_optin));
   CK(configure_setup_kernels(ctx->smem_optin));
 
   return PDHG_OK;
@@ -518,7 +550,7 @@ pdhg_status pdhg::alloc_arrays(pdhg_ctx* ctx) {
   CKS(dalloc(ctx, &ctx->D_c, n));
   const size_t es = elem(ctx);
   void** vecs_n[] = {&ctx->x, &ctx->x_avg, &ctx->x_last};
-  void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg};
+  void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg, &ctx->Ax_last};
   for (void** p : vecs_n) CKS(dalloc(ctx, (char**)p, es * n));
   for (void** p : vecs_m) CKS(dalloc(ctx, (char**)p, es * m));
   CKS(dalloc(ctx, &ctx->xs64, n));
@@ -568,7 +600,7 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
   const int64_t nnz = ctx->nnz, np = ctx->nnz_pad;
   const size_t es = elem(ctx);
   void** vecs_n[] = {&ctx->x, &ctx->x_avg, &ctx->x_last};
-  void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg};
+  void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg, &ctx->Ax_last};
   int32_t* flags = nullptr;
   int32_t *cnt = nullptr, *tmp = nullptr;
   CKS(dalloc(ctx, &flags, 1));
@@ -774,9 +806,11 @@ extern "C" pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const i
     pdhg_default_options(&ctx->opt);
   if (ctx->opt.eval_freq < 1 || ctx->opt.ruiz_iters < 0 || ctx->opt.power_max_iter < 0 ||
       (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED) ||
-      ctx->opt.tile_nnz < -8 || ctx->opt.tile_nnz > 8192) {
+      ctx->opt.tile_nnz < -8 || ctx->opt.tile_nnz > 8192 ||
+      (ctx->opt.method != 0 && ctx->opt.method != 1) ||
+      !(ctx->opt.reflection >= 0.0 && ctx->opt.reflection <= 1.0)) {
     set_error("invalid options (eval_freq >= 1, ruiz_iters >= 0, precision 0/1, "
-              "-8 <= tile_nnz <= 8192)");
+              "-8 <= tile_nnz <= 8192, method 0/1, 0 <= reflection <= 1)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }
@@ -1154,18 +1188,17 @@ extern "C" pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const doub
   CKS(state_in(ctx, ctx->y, y, m));
   CKS(state_in(ctx, ctx->y_avg, y_avg, m));
   CKS(state_in(ctx, ctx->y_last, y_last, m));
-  // caches A~x and A~x_avg in the iteration precision
-  if (ctx->mixed) {
-    launch_spmv<float>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val32, (const float*)ctx->x,
-                       (float*)ctx->Ax, ctx->l_dual, ctx->stream);
-    launch_spmv<float>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val32,
-                       (const float*)ctx->x_avg, (float*)ctx->Ax_avg, ctx->l_dual, ctx->stream);
-  } else {
-    launch_spmv<double>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64, (const double*)ctx->x,
-                        (double*)ctx->Ax, ctx->l_dual, ctx->stream);
-    launch_spmv<double>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64,
-                        (const double*)ctx->x_avg, (double*)ctx->Ax_avg, ctx->l_dual, ctx->stream);
+  // caches A~x, A~x_avg and A~x_last in the iteration precision
+  for (auto pr : {std::make_pair(ctx->x, ctx->Ax), std::make_pair(ctx->x_avg, ctx->Ax_avg),
+                  std::make_pair(ctx->x_last, ctx->Ax_last)}) {
+    if (ctx->mixed)
+      launch_spmv<float>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val32,
+                         (const float*)pr.first, (float*)pr.second, ctx->l_dual, ctx->stream);
+    else
+      launch_spmv<double>(ctx->sa.view, ctx->a_rp, ctx->a_col, ctx->a_val64,
+                          (const double*)pr.first, (double*)pr.second, ctx->l_dual, ctx->stream);
   }
+  ctx->launches += 3;
   Scalars hs;
   CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

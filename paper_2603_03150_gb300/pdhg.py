@@ -52,6 +52,8 @@ class Options(ctypes.Structure):
         ("tile_nnz", ctypes.c_int32),
         ("kernel_timing", ctypes.c_int32),
         ("verbose", ctypes.c_int32),
+        ("method", ctypes.c_int32),
+        ("reflection", ctypes.c_double),
     ]
 
 
@@ -164,7 +166,8 @@ class Solver:
                  eta_safety: float = 0.95, power_max_iter: int = 200,
                  power_rel_tol: float = 1e-10, device_io: bool = False, stream=None,
                  use_graphs: bool = True, autotune: bool = True, tile_nnz: int = 0,
-                 kernel_timing: bool = False):
+                 kernel_timing: bool = False, method: str = "averaged",
+                 reflection: float = 1.0):
         L = lib()
         o = Options()
         L.pdhg_default_options(ctypes.byref(o))
@@ -181,6 +184,10 @@ class Solver:
         o.autotune = 1 if autotune else 0
         o.tile_nnz = tile_nnz
         o.kernel_timing = 1 if kernel_timing else 0
+        if method not in ("averaged", "halpern"):
+            raise ValueError("method must be 'averaged' or 'halpern'")
+        o.method = 1 if method == "halpern" else 0
+        o.reflection = reflection
         self.m, self.n = int(m), int(n)
         self.device_io = device_io
         self.mixed = o.precision == FP32_MIXED
