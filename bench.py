@@ -210,7 +210,7 @@ def run_ours(args):
         src = devt if device_io else pinned
         s = pdhg.Solver(m, n, src["row_ptr"], src["col"], src["val"], src["b"], src["c"],
                         precision=precision, device_io=device_io, stream=stream.cuda_stream,
-                        kernel_timing=timing)
+                        kernel_timing=timing, method=args.method)
         st = s.solve(EPS, args.max_iter)
         g = s.get(out=outs[0] if outs else None)
         w = s.warmstart_point(unscaled=True, out=outs[1] if outs else None)
@@ -301,7 +301,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(lp, args.cpu_iters)
+        cpu = cpu_baseline(lp, args.cpu_iters, args.method)
 
     if rank == 0:
         ms_step = total_ms / max(len(rec), 1)
@@ -312,7 +312,8 @@ def run_ours(args):
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "precision": args.precision +
                        ("_mixed (f64 norms, gap, restart rule, step/weight updates)" if args.precision == "fp32" else ""),
-                       "eps_rel": EPS, "step": "create + solve to eps + get + warmstart_point",
+                       "eps_rel": EPS, "method": args.method,
+                       "step": "create + solve to eps + get + warmstart_point",
                        "l2": "flushed between steps (512 MiB write), inputs resident in HBM",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "schedule": rec[0]["sched"]},
@@ -465,14 +466,14 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(lp, iters):
+def cpu_baseline(lp, iters, method="averaged"):
     """The oracle as it stands, timed on this host: its set-up once (timed
     apart), then `iters` PDHG iterations (steady-state iterations per second)."""
     from oracle import pdhg_oracle as O
     t0 = time.perf_counter()
     S = O.setup(lp)
     t1 = time.perf_counter()
-    O.solve(lp, EPS, iters, S=S)
+    O.solve(lp, EPS, iters, opts=O.Options(method=method), S=S)
     t2 = time.perf_counter()
     return {"value": round(iters / (t2 - t1), 3), "unit": "iter/s", "cores": 1, "kind": "oracle",
             "sample": f"{iters} iterations of the float64 numpy/scipy oracle on the same LP after "
@@ -497,7 +498,7 @@ def run_reference(args):
     for i in range(args.warmup + args.steps):
         t = time.perf_counter()
         k += args.ref_iters
-        r = O.solve(lp, EPS, k, S=S, state=st)
+        r = O.solve(lp, EPS, k, opts=O.Options(method=args.method), S=S, state=st)
         st = r.state
         zs = np.maximum(0.0, S.c_t - S.At.T @ st.y)
         O.centered_start_point(st.x, zs)
@@ -529,6 +530,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="powerlaw")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--method", choices=["averaged", "halpern"], default="averaged",
+                    help="PDHG iteration: restarted averaged (default) or reflected Halpern")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=128)
     ap.add_argument("--ref-iters", type=int, default=64)
