@@ -466,6 +466,72 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Tolerance sweep (eps_rel = 1e-4, 1e-6, 1e-8) on one LP, FP64 plain and
+    FP32-mixed: time to the Section 2 test, iterations and the maximum
+    violation of the returned point on the original model (Section 4.3).
+    One warm-up and `--steps` timed solves per (precision, eps); the ratio of
+    each time to the eps = 1e-4 time is the shape of the paper's tradeoff."""
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2603_03150_gb300 import pdhg
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    lp = make_lp(args.workload)
+    devt = {k: torch.from_numpy(np.ascontiguousarray(getattr(lp, k))).to(dev)
+            for k in ["row_ptr", "col", "val", "b", "c"]}
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    launches = 0
+    with Clocks(local) as clk:
+        for prec in ("fp64", "fp32"):
+            rows = []
+            for eps in (1e-4, 1e-6, 1e-8):
+                ms, its, sts, viol = [], [], [], []
+                for i in range(1 + args.steps):
+                    with torch.cuda.stream(stream):
+                        flush.fill_(float(i))
+                    stream.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s = pdhg.Solver(lp.m, lp.n, devt["row_ptr"], devt["col"], devt["val"],
+                                    devt["b"], devt["c"], precision=prec, device_io=True,
+                                    stream=stream.cuda_stream, method=args.method)
+                    st = s.solve(eps, args.max_iter)
+                    s.get()
+                    e1.record(stream)
+                    stream.synchronize()
+                    info = s.info(violation=True)
+                    launches += s.launch_count()
+                    s.close()
+                    if i >= 1:
+                        ms.append(e0.elapsed_time(e1))
+                        its.append(info["iters"])
+                        sts.append(pdhg.STATUS_NAMES.get(st, st))
+                        viol.append(info["max_violation"])
+                rows.append(dict(eps_rel=eps, time_s=round(float(np.mean(ms)) / 1e3, 5),
+                                 iters=int(np.mean(its)), status=sts,
+                                 max_violation=float(np.max(viol))))
+            t0 = rows[0]["time_s"]
+            for r in rows:
+                r["time_vs_1e-4"] = round(r["time_s"] / t0, 3) if t0 > 0 else None
+            out[prec] = rows
+    value = out["fp64"][-1]["time_s"]
+    line = {"metric": "tolerance sweep: time to eps_rel and max violation (FP64, FP32-mixed)",
+            "value": value, "unit": "s (FP64, eps_rel = 1e-8)", "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "method": args.method,
+                       "step": "create + solve to eps + get", "max_iter": args.max_iter,
+                       "l2": "flushed between solves (512 MiB write)"},
+            "sweep": out, "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(lp, iters, method="averaged"):
     """The oracle as it stands, timed on this host: its set-up once (timed
     apart), then `iters` PDHG iterations (steady-state iterations per second)."""
@@ -538,11 +604,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER,
                     help="iteration cap per solve (profiling runs use a small cap)")
+    ap.add_argument("--eps-sweep", action="store_true",
+                    help="tolerance sweep 1e-4 / 1e-6 / 1e-8 on --workload (FP64 and FP32-mixed)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.eps_sweep:
+        if args.max_iter == MAX_ITER:
+            args.max_iter = 200_000  # FP32-mixed stalls above its precision: bound the sweep
+        run_sweep(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "adjoint":

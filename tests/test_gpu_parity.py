@@ -349,3 +349,25 @@ def test_kernel_timing_samples():
         s.solve(1e-6, 640)
         t = s.kernel_timing()
     assert t["samples"] >= 5 and t["primal_ms"] > 0 and t["dual_ms"] > 0
+
+
+# ----------------------------------------------------------------- tolerance sweep
+def test_tolerance_sweep_matches_oracle():
+    """eps_rel = 1e-4, 1e-6, 1e-8 (FP64): the oracle's iteration counts, the
+    maximum violation of the returned point (Section 4.3) as the oracle computes
+    it, and violations that shrink with eps."""
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+    viols = []
+    for eps in (1e-4, 1e-6, 1e-8):
+        r = O.solve(lp, eps, 200_000)
+        with pdhg.Solver.from_lp(lp) as s:
+            assert s.solve(eps, 200_000) == pdhg.PDHG_CONVERGED
+            g = s.get()
+            info = s.info()
+        assert info["iters"] == r.iters and info["restarts"] == r.restarts
+        mv = O.max_violation(A, lp.b, lp.c, g["x"], g["y"])
+        assert abs(info["max_violation"] - mv) <= 1e-9 * (1 + mv)
+        assert abs(info["max_violation"] - r.max_violation) <= 1e-7 * (1 + r.max_violation)
+        viols.append(info["max_violation"])
+    assert viols[2] < viols[0]
