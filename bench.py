@@ -42,7 +42,19 @@ WORKLOADS = {
               "5 nnz per column, LP i seeded i (sum m=617840, sum n=1544469, sum nnz=7722345)"),
     "adjoint": ("64 planted LPs m=2000 n=5000, 5 nnz per column, seeds 0..63, targets "
                 "U[0,1] seeded 1000+i; loss ||x - x_target||^2"),
+    "hybrid": ("15 LPs: planted m in {500, 1000, 2000} (n = 2.5m, 5 nnz per column) x seeds "
+               "0..2; transportation 20x30, 30x40, 40x60; power-law m=1000 n=5000 nnz=25000 "
+               "(seeds 0, 1) and m=2000 n=10000 nnz=60000 (seed 0)"),
 }
+
+
+def hybrid_lps():
+    from paper_2603_03150_gb300 import lpgen
+    lps = [lpgen.planted_lp(m, int(2.5 * m), seed=s) for m in (500, 1000, 2000) for s in range(3)]
+    lps += [lpgen.transportation_lp(a, b) for a, b in ((20, 30), (30, 40), (40, 60))]
+    lps += [lpgen.powerlaw_lp(m=1000, n=5000, nnz=25000, k_max=500, seed=s) for s in (0, 1)]
+    lps.append(lpgen.powerlaw_lp(m=2000, n=10000, nnz=60000, k_max=1000, seed=0))
+    return lps
 
 
 def make_lp(name):
@@ -532,6 +544,86 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hybrid(args):
+    """PDHG on the GPU to eps_rel = 1e-4 and 1e-6, Algorithm 1's start point
+    (scaled model) from the GPU, then the host interior-point method warm
+    (with the bump loop) and cold on the same scaled LP: success rate, the
+    geometric mean of warm/cold interior-point iterations over LPs both
+    solve, and how many solve in <= 10 iterations (the statistics of the
+    paper's Section 4.6 tables)."""
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import scipy.sparse as sp
+    from paper_2603_03150_gb300 import hybrid_ipm as H
+    from paper_2603_03150_gb300 import pdhg
+    torch.cuda.set_device(local)
+    prec = args.precision if args.precision_set else "fp64"
+    rows, launches = [], 0
+    with Clocks(local) as clk:
+        for lp in hybrid_lps():
+            A = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n))
+            row = {"lp": lp.name, "m": lp.m, "n": lp.n, "nnz": int(lp.nnz)}
+            scaled = None
+            for eps in (1e-4, 1e-6):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                with pdhg.Solver.from_lp(lp, precision=prec, method=args.method) as s:
+                    st = s.solve(eps, args.max_iter)
+                    xp, y, zp, _ = s.warmstart_point(unscaled=False)
+                    its = s.info(violation=False)["iters"]
+                    if scaled is None:
+                        sc = s.scaling()
+                        Dr, Dc = np.asarray(sc["D_r"]), np.asarray(sc["D_c"])
+                        scaled = (sp.diags(Dr) @ A @ sp.diags(Dc)).tocsr(), Dr * lp.b, Dc * lp.c
+                    launches += s.launch_count()
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                As, bs, cs = scaled
+                rw = H.warm_start(As, bs, cs, np.asarray(xp), np.asarray(y), np.asarray(zp))
+                t2 = time.perf_counter()
+                row[f"{eps:.0e}"] = {"pdhg_status": pdhg.STATUS_NAMES.get(st, st),
+                                     "pdhg_iters": its, "pdhg_s": round(t1 - t0, 4),
+                                     "ipm_status": rw["status"], "ipm_iters": rw["iters"],
+                                     "bumps": rw["bumps"], "ipm_s": round(t2 - t1, 3)}
+            t2 = time.perf_counter()
+            rc = H.mehrotra(*scaled)
+            row["cold"] = {"ipm_status": rc["status"], "ipm_iters": rc["iters"],
+                           "ipm_s": round(time.perf_counter() - t2, 3)}
+            rows.append(row)
+    summary = {}
+    cold_ok = [r for r in rows if r["cold"]["ipm_status"] == "optimal"]
+    summary["cold"] = {"tried": len(rows), "solved": len(cold_ok),
+                       "solved_in_10": sum(r["cold"]["ipm_iters"] <= 10 for r in cold_ok)}
+    for key in ("1e-04", "1e-06"):
+        tried = [r for r in rows if r[key]["pdhg_status"] == "converged"]
+        ok = [r for r in tried if r[key]["ipm_status"] == "optimal"]
+        both = [r for r in ok if r["cold"]["ipm_status"] == "optimal"]
+        ratio = (float(np.exp(np.mean([np.log(max(r[key]["ipm_iters"], 1) /
+                                              max(r["cold"]["ipm_iters"], 1)) for r in both])))
+                 if both else None)
+        summary[key] = {"tried": len(tried), "solved": len(ok),
+                        "success_rate": round(len(ok) / max(len(tried), 1), 3),
+                        "ipm_iteration_ratio_geomean": round(ratio, 3) if ratio else None,
+                        "solved_in_10": sum(r[key]["ipm_iters"] <= 10 for r in ok)}
+    line = {"metric": "IPM iterations warm (PDHG eps 1e-4 + Algorithm 1) / cold, geometric mean",
+            "value": summary["1e-04"]["ipm_iteration_ratio_geomean"], "unit": "ratio",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["hybrid"], "pdhg_precision": prec,
+                       "method": args.method, "ipm": "host Mehrotra predictor-corrector, dense "
+                       "normal equations, Section 2 test at 1e-8, scaled model",
+                       "algorithm1": "mu_min = alpha_min = 1e-6, delta_max = 1e-4, bump loop "
+                       "at first step < 1e-6"},
+            "summary": summary, "paper_section_4_6": {"1e-04": {"success_rate": [0.81, 0.83],
+                                                          "ipm_iteration_ratio": [0.51, 0.55]},
+                                                "1e-06": {"success_rate": [0.88, 0.87],
+                                                          "ipm_iteration_ratio": [0.30, 0.35]}},
+            "per_lp": rows, "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(lp, iters, method="averaged"):
     """The oracle as it stands, timed on this host: its set-up once (timed
     apart), then `iters` PDHG iterations (steady-state iterations per second)."""
@@ -607,10 +699,13 @@ def main():
     ap.add_argument("--eps-sweep", action="store_true",
                     help="tolerance sweep 1e-4 / 1e-6 / 1e-8 on --workload (FP64 and FP32-mixed)")
     args = ap.parse_args()
+    args.precision_set = any(a.startswith("--precision") for a in sys.argv[1:])
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "hybrid":
+        run_hybrid(args)
     elif args.eps_sweep:
         if args.max_iter == MAX_ITER:
             args.max_iter = 200_000  # FP32-mixed stalls above its precision: bound the sweep
