@@ -20,6 +20,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -108,7 +109,9 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples beside the run (the summary goes into the JSON line)
+        out_dir = os.environ.get("PDHG_BENCH_OUT", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
