@@ -101,11 +101,19 @@ void launch_segsort(int nseg, const int32_t* seg_ptr, int32_t* keys, double* val
 // row pointer rp
 void launch_window_words(const Tile* tiles, int ntiles, const int32_t* rp, int e, uint32_t* wd,
                          cudaStream_t s);
+// How a row statistic pass is split: `lanes` per row (4..32, from the mean
+// row length) and the rows longer than long_len (device ids), one block each.
+struct RowStatPlan {
+  int lanes = 32;
+  int long_len = 1 << 30;
+  const int32_t* long_ids = nullptr;
+  int nlong = 0;
+};
 // Ruiz / Pock-Chambolle statistic of each row of D_self M D_other:
 // mode 0: sqrt(max |.|), mode 1: sqrt(sum |.|); zero -> 1.
 void launch_row_stat(int nrows, const int32_t* rp, const int32_t* col, const double* val,
                      const double* d_self, const double* d_other, int mode, double* out,
-                     cudaStream_t s);
+                     const RowStatPlan& plan, cudaStream_t s);
 void launch_div(double* d, const double* r, int len, cudaStream_t s);
 void launch_fill(double* d, double v, int64_t len, cudaStream_t s);
 // A~_ij = (D_r[i] A_ij) D_c[j]; transposed = 1 when the rows are columns of A

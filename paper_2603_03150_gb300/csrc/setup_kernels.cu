@@ -252,33 +252,89 @@ void launch_segsort(int nseg, const int32_t* seg_ptr, int32_t* keys, double* val
 // ---------------------------------------------------------------------------
 // scaling statistics of D_self M D_other and scaled copies
 // ---------------------------------------------------------------------------
-__global__ void k_row_stat(int nrows, const int32_t* rp, const int32_t* col, const double* val,
-                           const double* d_self, const double* d_other, int mode, double* out) {
-  const int lane = threadIdx.x & 31;
+// Row statistic sqrt(d_self[i] * max_j |M_ij| d_other[j]) (mode 0) or
+// sqrt(d_self[i] * sum_j |M_ij| d_other[j]) (mode 1); zero -> 1.  G lanes per
+// row (G sized to the mean row length, every lane of a warp takes part in the
+// shuffles); rows longer than long_len are left to k_row_stat_long.
+template <int G>
+__global__ void k_row_stat(int nrows, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ d_self,
+                           const double* __restrict__ d_other, int mode, int long_len,
+                           double* __restrict__ out) {
+  constexpr int RPW = 32 / G;  // rows per warp and pass
+  const int lane = threadIdx.x & 31, gw = lane / G, gl = lane & (G - 1);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int i = warp; i < nrows; i += nw) {
+  for (int base = warp * RPW; base < nrows; base += nw * RPW) {
+    const int i = base + gw;
     double acc = 0.0;
-    for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) {
-      const double a = fabs(val[k]) * d_other[col[k]];
-      acc = mode ? acc + a : fmax(acc, a);
+    bool mine = false;
+    if (i < nrows) {
+      const int b = rp[i], e = rp[i + 1];
+      if (e - b <= long_len) {
+        mine = true;
+        for (int k = b + gl; k < e; k += G) {
+          const double a = fabs(val[k]) * d_other[col[k]];
+          acc = mode ? acc + a : fmax(acc, a);
+        }
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double t = __shfl_down_sync(0xffffffffu, acc, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const double t = __shfl_down_sync(0xffffffffu, acc, o, G);
       acc = mode ? acc + t : fmax(acc, t);
     }
-    if (lane == 0) {
+    if (mine && gl == 0) {
       const double r = sqrt(d_self[i] * acc);
       out[i] = (r == 0.0) ? 1.0 : r;
     }
   }
 }
+
+// the same statistic for the rows listed in ids, one block of 256 per row
+__global__ void k_row_stat_long(const int32_t* __restrict__ ids, const int32_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, const double* __restrict__ val,
+                                const double* __restrict__ d_self,
+                                const double* __restrict__ d_other, int mode,
+                                double* __restrict__ out) {
+  __shared__ double red[8];
+  const int i = ids[blockIdx.x];
+  double acc = 0.0;
+  for (int k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) {
+    const double a = fabs(val[k]) * d_other[col[k]];
+    acc = mode ? acc + a : fmax(acc, a);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_down_sync(0xffffffffu, acc, o);
+    acc = mode ? acc + t : fmax(acc, t);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = red[0];
+    for (int w = 1; w < 8; ++w) v = mode ? v + red[w] : fmax(v, red[w]);
+    const double r = sqrt(d_self[i] * v);
+    out[i] = (r == 0.0) ? 1.0 : r;
+  }
+}
+
 void launch_row_stat(int nrows, const int32_t* rp, const int32_t* col, const double* val,
                      const double* d_self, const double* d_other, int mode, double* out,
-                     cudaStream_t s) {
-  k_row_stat<<<grid_cap((int64_t)nrows * 32), 256, 0, s>>>(nrows, rp, col, val, d_self, d_other,
-                                                          mode, out);
+                     const RowStatPlan& plan, cudaStream_t s) {
+  const int g = grid_cap((int64_t)nrows * plan.lanes);
+#define PDHG_ROW_STAT(G) \
+  k_row_stat<G><<<g, 256, 0, s>>>(nrows, rp, col, val, d_self, d_other, mode, plan.long_len, out)
+  switch (plan.lanes) {
+    case 4: PDHG_ROW_STAT(4); break;
+    case 8: PDHG_ROW_STAT(8); break;
+    case 16: PDHG_ROW_STAT(16); break;
+    default: PDHG_ROW_STAT(32); break;
+  }
+#undef PDHG_ROW_STAT
+  if (plan.nlong > 0)
+    k_row_stat_long<<<plan.nlong, 256, 0, s>>>(plan.long_ids, rp, col, val, d_self, d_other, mode,
+                                              out);
 }
 
 __global__ void k_fill(double* d, double v, int64_t len) {

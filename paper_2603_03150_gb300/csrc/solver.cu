@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -654,6 +655,30 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
   CK(cudaGetLastError());
 
   // a2: Ruiz (infinity norm) then Pock-Chambolle (alpha = 1)
+  RowStatPlan plan_a, plan_t;
+  {
+    constexpr int kLongRow = 1024;
+    auto make_plan = [&](const std::vector<int32_t>& rp, int nrows, RowStatPlan* pl) -> pdhg_status {
+      const double mean = nrows > 0 ? (double)rp[nrows] / nrows : 0.0;
+      pl->lanes = mean <= 6 ? 4 : mean <= 12 ? 8 : mean <= 24 ? 16 : 32;
+      pl->long_len = kLongRow;
+      std::vector<int32_t> ids;
+      for (int i = 0; i < nrows; ++i)
+        if (rp[i + 1] - rp[i] > kLongRow) ids.push_back(i);
+      pl->nlong = (int)ids.size();
+      if (!ids.empty()) {
+        int32_t* d = nullptr;
+        CKS(dalloc(ctx, &d, ids.size()));
+        CK(cudaMemcpyAsync(d, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));  // ids is a local vector
+        pl->long_ids = d;
+      }
+      return PDHG_OK;
+    };
+    CKS(make_plan(ctx->h_a_rp, m, &plan_a));
+    CKS(make_plan(ctx->h_t_rp, n, &plan_t));
+  }
   double *r = ctx->out_m1, *s = ctx->out_n1;
   launch_fill(ctx->D_r, 1.0, m, ctx->stream);
   launch_fill(ctx->D_c, 1.0, n, ctx->stream);
@@ -661,9 +686,9 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
   for (int it = 0; it < rounds; ++it) {
     const int mode = it < ctx->opt.ruiz_iters ? 0 : 1;
     launch_row_stat(m, ctx->a_rp, ctx->a_col, ctx->a_val_orig, ctx->D_r, ctx->D_c, mode, r,
-                    ctx->stream);
+                    plan_a, ctx->stream);
     launch_row_stat(n, ctx->t_rp, ctx->t_col, ctx->t_val_orig, ctx->D_c, ctx->D_r, mode, s,
-                    ctx->stream);
+                    plan_t, ctx->stream);
     launch_div(ctx->D_r, r, m, ctx->stream);
     launch_div(ctx->D_c, s, n, ctx->stream);
   }
@@ -673,7 +698,8 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
                     ctx->t_val64, ctx->t_val32, ctx->stream);
   launch_scale_vec(m, ctx->D_r, ctx->b, ctx->b_t64, ctx->b_t32, ctx->stream);
   launch_scale_vec(n, ctx->D_c, ctx->c, ctx->c_t64, ctx->c_t32, ctx->stream);
-  ctx->launches += 2 + 4LL * rounds + 4;
+  ctx->launches += 2 + 4LL * rounds + 4 +
+                   (long long)rounds * ((plan_a.nlong > 0) + (plan_t.nlong > 0));
   CK(cudaGetLastError());
 
   // zero state (also what the autotuner multiplies)
@@ -683,10 +709,27 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
+// With options.verbose: the wall time of each create stage on stderr (the
+// stream is synchronised at every stage boundary, so it costs a little).
+struct StageClock {
+  pdhg_ctx* ctx;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), last = t0;
+  void operator()(const char* name) {
+    if (!ctx->opt.verbose) return;
+    cudaStreamSynchronize(ctx->stream);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "pdhg_create: %-24s %9.3f ms\n", name,
+                 std::chrono::duration<double, std::milli>(now - last).count());
+    last = now;
+  }
+};
+
 static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int32_t* col,
                                const double* val, const double* b, const double* c) {
   const int m = ctx->m, n = ctx->n;
+  StageClock stage{ctx};
   CKS(setup_device(ctx));
+  stage("device set-up");
   // row pointer on the host (scheduler) and its checks
   ctx->h_a_rp.resize((size_t)m + 1);
   if (ctx->opt.io_on_device) {
@@ -707,12 +750,17 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     }
   ctx->nnz = ctx->h_a_rp[m];
 
+  stage("row pointer checks");
   CKS(alloc_arrays(ctx));
+  stage("allocation");
   CKS(upload_lp(ctx, col, val, b, c));
+  stage("upload");
   CKS(prepare_matrix(ctx));
+  stage("validate/transpose/scale");
 
   // float64 schedules (the iteration schedules are tuned once the scalars exist)
   CKS(fixed_schedules(ctx));
+  stage("float64 schedules");
 
   // a3: power iteration on A~^T A~ (float64)
   {
@@ -735,6 +783,7 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     }
     CK(cudaGetLastError());
   }
+  stage("power iteration");
 
   // norms, omega_0, tau, sigma, first restart point
   {
@@ -766,8 +815,11 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     ctx->power_iters = hp.k;
   }
 
+  stage("scalars");
   CKS(tune_schedules(ctx));
+  stage("schedule tuning");
   CKS(polling_resources(ctx));
+  stage("polling resources");
   return PDHG_OK;
 }
 

@@ -167,7 +167,7 @@ class Solver:
                  power_rel_tol: float = 1e-10, device_io: bool = False, stream=None,
                  use_graphs: bool = True, autotune: bool = True, tile_nnz: int = 0,
                  kernel_timing: bool = False, method: str = "averaged",
-                 reflection: float = 1.0):
+                 reflection: float = 1.0, verbose: bool = False):
         L = lib()
         o = Options()
         L.pdhg_default_options(ctypes.byref(o))
@@ -188,6 +188,7 @@ class Solver:
             raise ValueError("method must be 'averaged' or 'halpern'")
         o.method = 1 if method == "halpern" else 0
         o.reflection = reflection
+        o.verbose = 1 if verbose else 0
         self.m, self.n = int(m), int(n)
         self.device_io = device_io
         self.mixed = o.precision == FP32_MIXED
