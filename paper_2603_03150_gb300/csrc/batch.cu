@@ -839,13 +839,8 @@ static pdhg_status tune_batch_schedules(pdhg_ctx* ctx) {
     const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
     const int nrows = on_a ? ctx->m : ctx->n;
     const int64_t* off = on_a ? ctx->h_m_off.data() : ctx->h_n_off.data();
-    int64_t longest = 0;
-    for (int r = 0; r < nrows; ++r) longest = std::max<int64_t>(longest, rp[r + 1] - rp[r]);
     std::vector<int> cands = {kFixedE};
-    if (ctx->opt.autotune) {
-      cands = {8, 16, 32};
-      if (longest <= 256) cands.insert(cands.end(), {-4, -8});
-    }
+    if (ctx->opt.autotune) cands = {8, 16, 32};  // vector variants: never faster (measured)
     DevSched best = on_a ? ctx->sa8 : ctx->st8;
     int32_t* best_lp = on_a ? ctx->lp_a8_tiles : ctx->lp_t8_tiles;
     float best_ms = 1e30f;
@@ -877,6 +872,9 @@ static pdhg_status tune_batch_schedules(pdhg_ctx* ctx) {
           CKS(time_batch_kernel<double>(ctx, on_a, &ms));
       }
       const float bias = (e == 8) ? 0.97f : 1.0f;
+      if (ctx->opt.verbose)
+        std::fprintf(stderr, "pdhg_create: tune %s variant %3d: %8.4f ms\n",
+                     on_a ? "A  " : "A^T", e, ms);
       if (ms * bias < best_ms) {
         best_ms = ms * bias;
         best = d;
@@ -909,8 +907,10 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
                                      const int32_t* row_ptr, const int32_t* col,
                                      const double* val, const double* b, const double* c) {
   const int count = ctx->count;
+  StageClock stage{ctx};
   CKS(setup_device(ctx));
   CK(configure_batch_kernels(ctx->smem_optin));
+  stage("device set-up");
   // offsets and the stacked row pointer on the host
   ctx->h_m_off.assign(count + 1, 0);
   ctx->h_n_off.assign(count + 1, 0);
@@ -981,7 +981,9 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
     set_error("invalid batch: a column index is outside its LP's [0, n)");
     return PDHG_INVALID_ARG;
   }
+  stage("checks/allocation/upload");
   CKS(prepare_matrix(ctx));
+  stage("validate/transpose/scale");
 
   // LP-aligned float64 schedules (set-up, report, adjoint); the iteration
   // schedules start as the same and are tuned once the scalars exist
@@ -1052,13 +1054,16 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
     }
     CK(cudaGetLastError());
   }
+  stage("power iteration");
   k_binit<kBlock><<<count, kBlock, 0, ctx->stream>>>(ctx->sc, ctx->ps, d_m_off, d_n_off, ctx->b,
                                                      ctx->c, ctx->b_t64, ctx->c_t64,
                                                      ctx->opt.eta_safety);
   ctx->launches += 1;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
+  stage("scalars");
   CKS(tune_batch_schedules(ctx));
+  stage("schedule tuning");
   CKS(polling_resources(ctx));
   return PDHG_OK;
 }

@@ -2,6 +2,8 @@
 // translation units of the C ABI.
 #pragma once
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <string>
 #include <vector>
 
@@ -136,6 +138,21 @@ struct pdhg_ctx {
 };
 
 namespace pdhg {
+
+// With options.verbose: the wall time of each create stage on stderr (the
+// stream is synchronised at every stage boundary, so it costs a little).
+struct StageClock {
+  pdhg_ctx* ctx;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), last = t0;
+  void operator()(const char* name) {
+    if (!ctx->opt.verbose) return;
+    cudaStreamSynchronize(ctx->stream);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "pdhg_create: %-24s %9.3f ms\n", name,
+                 std::chrono::duration<double, std::milli>(now - last).count());
+    last = now;
+  }
+};
 
 template <typename T>
 pdhg_status dalloc(pdhg_ctx* ctx, T** p, size_t count) {

@@ -394,8 +394,9 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
     else if (tn > 0)
       cands.push_back({tn <= 2044 ? 8 : (tn <= 4092 ? 16 : 32), tn});
     else if (ctx->opt.autotune) {
+      // the vector variants were slower than E = 8 on every measured matrix
+      // since the window words; they stay available through tile_nnz < 0
       cands = {{8, 0}, {16, 0}, {32, 0}};
-      if (longest <= 256) cands.insert(cands.end(), {{-4, 0}, {-8, 0}});
     } else {
       cands = {{8, 0}};
     }
@@ -425,6 +426,9 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
           CKS(time_iteration_kernel<double>(ctx, on_a, &ms));
       }
       const float bias = (e == 8) ? 0.97f : 1.0f;
+      if (ctx->opt.verbose)
+        std::fprintf(stderr, "pdhg_create: tune %s variant %3d cap %5d: %8.4f ms\n",
+                     on_a ? "A  " : "A^T", e, d.view.tile_nnz, ms);
       if (ms * bias < best_ms) {
         best_ms = ms * bias;
         best = d;
@@ -708,21 +712,6 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
 
   return PDHG_OK;
 }
-
-// With options.verbose: the wall time of each create stage on stderr (the
-// stream is synchronised at every stage boundary, so it costs a little).
-struct StageClock {
-  pdhg_ctx* ctx;
-  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), last = t0;
-  void operator()(const char* name) {
-    if (!ctx->opt.verbose) return;
-    cudaStreamSynchronize(ctx->stream);
-    const auto now = std::chrono::steady_clock::now();
-    std::fprintf(stderr, "pdhg_create: %-24s %9.3f ms\n", name,
-                 std::chrono::duration<double, std::milli>(now - last).count());
-    last = now;
-  }
-};
 
 static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int32_t* col,
                                const double* val, const double* b, const double* c) {
