@@ -164,6 +164,9 @@ __device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
   return r;
 }
 
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
   float v[4];

@@ -234,7 +234,7 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
     const int w0 = (nzb & ~3) + tid * E;
     const W d = tl.split < 0 ? ld_stream(wd + tl.word0 + tid, pol) : W(0);
 
-    // load, gather and walk; products outside [nzb, nze) are zero and carry
+    // load, gather and walk; nonzeros outside [nzb, nze) add zero and carry
     // no mask bit (split chunks have no mask bits: acc is the window's sum)
     int r = (int)(d >> (MB + 1));
     bool head = (d >> MB) & 1u;
@@ -269,18 +269,20 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
           }
         }
       }
-      T p[NV][EC];
+      // gathered values, zero outside [nzb, nze): the walk then accumulates
+      // with one fused multiply-add per nonzero
+      T gv[NV][EC];
 #pragma unroll
       for (int e = 0; e < EC; ++e) {
         const int k = wc + e;
         const bool in = k >= nzb && k < nze;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) p[v][e] = in ? vv[e] * __ldg(g.v[v] + cidx[e]) : T(0);
+        for (int v = 0; v < NV; ++v) gv[v][e] = in ? __ldg(g.v[v] + cidx[e]) : T(0);
       }
 #pragma unroll
       for (int e = 0; e < EC; ++e) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += p[v][e];
+        for (int v = 0; v < NV; ++v) acc[v] = fmadd(vv[e], gv[v][e], acc[v]);
         if ((d >> (c * EC + e)) & 1u) {
           if (head) {
             head_row = r;
