@@ -115,6 +115,33 @@ __device__ __forceinline__ void block_sum(const double (&v)[NQ], double (&out)[N
   __syncthreads();
 }
 
+// Sum of NQ-vectors stored one after another: parts a[0..na) then b[0..nb)
+// (entry p holds NQ doubles), computed by every thread of one block in a
+// fixed order: thread t sums entries t / NQ, t / NQ + BLOCK / NQ, ... of
+// quantity t % NQ, then the threads of a quantity are combined by a fixed
+// shuffle tree and the warps in order.  NQ a power of two <= 32 dividing
+// BLOCK.  The result is in out[0..NQ) (shared) after the final barrier.
+template <int BLOCK, int NQ>
+__device__ __forceinline__ void parts_sum(const double* a, int na, const double* b, int nb,
+                                          double* out, double* red) {
+  static_assert(NQ >= 1 && NQ <= 32 && (NQ & (NQ - 1)) == 0 && BLOCK % 32 == 0, "NQ");
+  constexpr int L = BLOCK / NQ;
+  const int t = threadIdx.x, q = t % NQ, lane = t & 31, w = t >> 5;
+  double s = 0.0;
+  for (int p = t / NQ; p < na + nb; p += L)
+    s += p < na ? __ldcg(a + (size_t)p * NQ + q) : __ldcg(b + (size_t)(p - na) * NQ + q);
+#pragma unroll
+  for (int o = 16; o >= NQ; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane < NQ) red[w * NQ + lane] = s;
+  __syncthreads();
+  if (t < NQ) {
+    double v = 0.0;
+    for (int i = 0; i < BLOCK / 32; ++i) v += red[i * NQ + t];
+    out[t] = v;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Loads of the matrix stream (column indices, values, window words): read
 // once per SpMV, so they carry an L2 evict-first policy and skip L1, leaving

@@ -172,13 +172,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  if (threadIdx.x < kEvalQ) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(B.partials + (size_t)b * kEvalQ + threadIdx.x);
-    for (int gi = 0; gi < B.t_sched.ngroups; ++gi) s += __ldcg(B.split_q + (size_t)gi * kEvalQ + threadIdx.x);
-    tot[threadIdx.x] = s;
-  }
-  __syncthreads();
+  parts_sum<BLOCK, kEvalQ>(B.partials, (int)gridDim.x, B.split_q, B.t_sched.ngroups, tot, red);
   if (threadIdx.x == 0) {
     B.sc->ticket = 0;
     apply_eval_rule(*B.sc, tot, chunk, B.log_k, B.log_flags, B.log_kkt);

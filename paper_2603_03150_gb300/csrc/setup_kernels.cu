@@ -496,13 +496,12 @@ __global__ void __launch_bounds__(BLOCK) k_pow_ATu(SchedView S, const int32_t* r
     is_last = (atomicAdd(&ps->ticket, 1) == (int)gridDim.x - 1);
   }
   __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
+  if (!is_last) return;
   __threadfence();
-  double lam = 0.0, nw2 = 0.0;
-  for (int b = 0; b < (int)gridDim.x + ngroups; ++b) {
-    lam += __ldcg(partials + 2 * b);
-    nw2 += __ldcg(partials + 2 * b + 1);
-  }
+  __shared__ double tot[2];
+  parts_sum<BLOCK, 2>(partials, (int)gridDim.x + ngroups, nullptr, 0, tot, red);
+  if (threadIdx.x != 0) return;
+  const double lam = tot[0], nw2 = tot[1];
   ps->ticket = 0;
   ps->k += 1;
   ps->lam = lam;
