@@ -191,6 +191,15 @@ __device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
   return r;
 }
 
+// Programmatic dependent launch: a half-step kernel launched with the
+// programmatic-serialization attribute may become resident while the kernel
+// before it drains; it lets its own successor do the same, then waits for
+// its predecessor's completion (and memory) before reading anything.
+// Launched without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
 

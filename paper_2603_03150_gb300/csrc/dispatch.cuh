@@ -31,6 +31,24 @@
 
 namespace pdhg {
 
+// Launch with programmatic stream serialization (the kernel must start with
+// pdl_enter(): it may begin while the previous kernel on the stream drains).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // raises a kernel's dynamic shared-memory limit to what the device allows
 // next to its static shared memory
 inline cudaError_t set_max_dyn_smem(const void* f, size_t max_smem) {

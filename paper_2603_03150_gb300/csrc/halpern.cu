@@ -34,6 +34,7 @@ struct HalpernPrimalEpi {
 
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_hprimal(IterBuffers<T> B, int i) {
+  pdl_enter();
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const long long tt = B.sc->t + i;  // iterations since restart before this one
@@ -66,6 +67,7 @@ struct HalpernDualEpi {
 
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_hdual(IterBuffers<T> B, int i) {
+  pdl_enter();
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const long long tt = B.sc->t + i;
@@ -78,11 +80,11 @@ __global__ void __launch_bounds__(BLOCK) k_hdual(IterBuffers<T> B, int i) {
 
 template <typename T>
 void launch_hprimal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s) {
-  PDHG_DISPATCH_E(B.t_sched.e, k_hprimal<T, kBlock, E_><<<L.grid, kBlock, L.smem, s>>>(B, i));
+  PDHG_DISPATCH_E(B.t_sched.e, launch_pdl(k_hprimal<T, kBlock, E_>, L.grid, kBlock, L.smem, s, B, i));
 }
 template <typename T>
 void launch_hdual(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s) {
-  PDHG_DISPATCH_E(B.a_sched.e, k_hdual<T, kBlock, E_><<<L.grid, kBlock, L.smem, s>>>(B, i));
+  PDHG_DISPATCH_E(B.a_sched.e, launch_pdl(k_hdual<T, kBlock, E_>, L.grid, kBlock, L.smem, s, B, i));
 }
 template void launch_hprimal<float>(const IterBuffers<float>&, const Launch&, int, cudaStream_t);
 template void launch_hprimal<double>(const IterBuffers<double>&, const Launch&, int, cudaStream_t);

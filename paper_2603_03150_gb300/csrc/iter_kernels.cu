@@ -30,6 +30,7 @@ struct PrimalEpi {
 
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_primal(IterBuffers<T> B, int i) {
+  pdl_enter();
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const long long tt = B.sc->t + i;  // iterations since restart before this one
@@ -63,6 +64,7 @@ struct DualEpi {
 
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_dual(IterBuffers<T> B, int i) {
+  pdl_enter();
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const long long tt = B.sc->t + i;
@@ -212,11 +214,11 @@ __global__ void k_restart(IterBuffers<T> B) {
 
 template <typename T>
 void launch_primal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s) {
-  PDHG_DISPATCH_E(B.t_sched.e, k_primal<T, kBlock, E_><<<L.grid, kBlock, L.smem, s>>>(B, i));
+  PDHG_DISPATCH_E(B.t_sched.e, launch_pdl(k_primal<T, kBlock, E_>, L.grid, kBlock, L.smem, s, B, i));
 }
 template <typename T>
 void launch_dual(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s) {
-  PDHG_DISPATCH_E(B.a_sched.e, k_dual<T, kBlock, E_><<<L.grid, kBlock, L.smem, s>>>(B, i));
+  PDHG_DISPATCH_E(B.a_sched.e, launch_pdl(k_dual<T, kBlock, E_>, L.grid, kBlock, L.smem, s, B, i));
 }
 template <typename T>
 void launch_eval(const IterBuffers<T>& B, const Launch& L, int chunk, cudaStream_t s) {
