@@ -371,3 +371,39 @@ def test_tolerance_sweep_matches_oracle():
         assert abs(info["max_violation"] - r.max_violation) <= 1e-7 * (1 + r.max_violation)
         viols.append(info["max_violation"])
     assert viols[2] < viols[0]
+
+
+# ----------------------------------------------------------------- no optimum
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["infeasible", "unbounded"])
+def test_lp_without_optimum_ends_cleanly(kind, precision):
+    """PDHG (this reading) has no infeasibility certificate: an LP without an
+    optimum runs to the iteration limit or stops on a non-finite evaluation,
+    never faults, and the context stays usable (get and the warm-start point
+    answer; a second solve call continues)."""
+    rng = np.random.default_rng(3)
+    m, n = 30, 80
+    D = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.3)
+    if kind == "infeasible":
+        D[0, :] = np.abs(D[0, :]) + 0.1      # sum of positive terms ...
+        b = np.abs(rng.standard_normal(m))
+        b[0] = -1.0                           # ... equal to -1: no x >= 0
+        c = rng.uniform(0.5, 2.0, n)
+    else:
+        D[:, 0] = 0.0                         # column 0 free of constraints
+        D[0, 0] = 0.0
+        x0 = rng.uniform(0.5, 1.0, n)
+        b = D @ x0
+        c = rng.uniform(0.5, 2.0, n)
+        c[0] = -1.0                           # and of negative cost: unbounded
+    A = sp.csr_matrix(D)
+    lp = lpgen.LP(m, n, A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.copy(), b, c)
+    with pdhg.Solver.from_lp(lp, precision=precision) as s:
+        st = s.solve(1e-6, 3000)
+        assert st in (pdhg.PDHG_MAX_ITER, pdhg.PDHG_NUMERICAL_ERROR)
+        g = s.get()
+        assert g["x"].shape == (n,)
+        s.warmstart_point()
+        st2 = s.solve(1e-6, 3200)
+        assert st2 in (pdhg.PDHG_MAX_ITER, pdhg.PDHG_NUMERICAL_ERROR)
+        assert s.info(violation=False)["iters"] <= 3200
