@@ -351,7 +351,7 @@ static void enqueue_chunk_any(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
 // (rows of A~^T) or dual (rows of A~) kernel on the initial state; the state
 // is zeroed again afterwards.  e > 0: segmented kernel with e nonzeros per
 // thread; e < 0: vector kernel with -e lanes per row (only if all rows are
-// short).  E = 8 is kept unless another choice is more than 3% faster, so
+// short).  E = 8 is kept unless another choice is more than 5% faster, so
 // timing noise does not flip the schedule from one context to the next.
 template <typename T>
 static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out) {
@@ -425,7 +425,7 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
         else
           CKS(time_iteration_kernel<double>(ctx, on_a, &ms));
       }
-      const float bias = (e == 8) ? 0.97f : 1.0f;
+      const float bias = (e == 8) ? 0.95f : 1.0f;
       if (ctx->opt.verbose)
         std::fprintf(stderr, "pdhg_create: tune %s variant %3d cap %5d: %8.4f ms\n",
                      on_a ? "A  " : "A^T", e, d.view.tile_nnz, ms);
