@@ -166,9 +166,15 @@ def peaks():
 
 
 def kernel_source_sha():
+    """Hash of the iteration kernels' sources with comments and blank space
+    removed (a comment edit does not invalidate a measurement)."""
+    import re
     h = hashlib.sha256()
     for f in ["spmv_tile.cuh", "iter_kernels.cu", "common.cuh"]:
-        h.update(open(os.path.join(ROOT, "paper_2603_03150_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2603_03150_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

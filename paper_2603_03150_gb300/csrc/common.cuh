@@ -203,29 +203,18 @@ __device__ __forceinline__ void pdl_enter() {
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
 
+// four consecutive values of the matrix stream (16- or 32-byte aligned)
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
   float v[4];
-  __device__ __forceinline__ void load(const float* p) {
-    float4 t = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-  }
   __device__ __forceinline__ void load_stream(const float* p, uint64_t pol) {
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
         : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
         : "l"(p), "l"(pol));
   }
-  __device__ __forceinline__ void store_smem(float* p) const {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  }
 };
 template <> struct Vec4<double> {
   double v[4];
-  __device__ __forceinline__ void load(const double* p) {
-    double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-  }
   __device__ __forceinline__ void load_stream(const double* p, uint64_t pol) {
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
         : "=d"(v[0]), "=d"(v[1])
@@ -234,14 +223,6 @@ template <> struct Vec4<double> {
         : "=d"(v[2]), "=d"(v[3])
         : "l"(p + 2), "l"(pol));
   }
-  __device__ __forceinline__ void store_smem(double* p) const {
-    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-  }
 };
-
-__device__ __forceinline__ int4 ldg_int4(const int32_t* p) {
-  return __ldg(reinterpret_cast<const int4*>(p));
-}
 
 }  // namespace pdhg

@@ -177,8 +177,6 @@ size_t smem_for(int kind, bool mixed, int max_rows, int e);
 pdhg_status upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d, const int32_t* rp);
 Launch make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int ntiles);
 size_t elem(const pdhg_ctx* ctx);
-// mean duration of a plain SpMV over schedule d (A when on_a, else A^T)
-pdhg_status time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float* ms_out);
 // create stages shared by the single-LP and batched paths
 pdhg_status setup_device(pdhg_ctx* ctx);
 pdhg_status alloc_arrays(pdhg_ctx* ctx);

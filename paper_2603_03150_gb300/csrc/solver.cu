@@ -194,43 +194,6 @@ Launch pdhg::make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int nt
   return Launch{std::max(grid, 1), smem};
 }
 
-// Time one SpMV schedule candidate (mean of a few launches after warm-up).
-pdhg_status pdhg::time_spmv(pdhg_ctx* ctx, const DevSched& d, bool on_a, float* ms_out) {
-  const size_t smem = smem_for(0, ctx->mixed, d.view.max_rows, d.view.e);
-  Launch L = make_launch(ctx, ctx->mixed ? 6 : 7, d.view.e, smem, d.view.ntiles);
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  const int warm = 3, reps = 10;
-  ctx->launches += warm + reps;
-  for (int it = 0; it < warm + reps; ++it) {
-    if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
-    if (ctx->mixed) {
-      if (on_a)
-        launch_spmv<float>(d.view, ctx->a_rp, ctx->a_col, ctx->a_val32, (const float*)ctx->x,
-                           (float*)ctx->Ax, L, ctx->stream);
-      else
-        launch_spmv<float>(d.view, ctx->t_rp, ctx->t_col, ctx->t_val32, (const float*)ctx->y,
-                           (float*)ctx->x_last, L, ctx->stream);
-    } else {
-      if (on_a)
-        launch_spmv<double>(d.view, ctx->a_rp, ctx->a_col, ctx->a_val64, (const double*)ctx->x,
-                            (double*)ctx->Ax, L, ctx->stream);
-      else
-        launch_spmv<double>(d.view, ctx->t_rp, ctx->t_col, ctx->t_val64, (const double*)ctx->y,
-                            (double*)ctx->x_last, L, ctx->stream);
-    }
-  }
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(e1, ctx->stream));
-  CK(cudaEventSynchronize(e1));
-  float ms = 0;
-  CK(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  *ms_out = ms / reps;
-  return PDHG_OK;
-}
 
 // Float64 schedules (report, Algorithm 1, power iteration) and reduction
 // scratch sized for any iteration schedule the tuner may pick.

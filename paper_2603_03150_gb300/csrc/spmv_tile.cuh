@@ -3,15 +3,17 @@
 // A tile is a run of whole rows holding at most BLOCK*E - 4 nonzeros, or one
 // chunk of a row too long for a tile ("split row"), or a run of rows without
 // nonzeros.  Per tile of whole rows:
-//  (1) thread t loads the E consecutive nonzeros of the window
-//      [a + tE, a + tE + E), a = the tile start rounded down to 16 bytes,
-//      with 128-bit loads of column indices and values, and issues all E
-//      gathers v[col] back to back (products stay in registers);
-//  (2) the thread walks the row ends inside its window, read from a 32-bit
-//      window word computed once with the schedule (row-end mask, first row,
-//      "continues a row" bit): rows that end there are finished at once, the
-//      first one with a carry-in if it began in an earlier window, and the row
-//      still open at the window's end is carried out;
+//  (1) thread t owns the E consecutive nonzeros of the window
+//      [a + tE, a + tE + E), a = the tile start rounded down to 16 bytes; in
+//      steps of 8 it loads column indices and values with 128-bit loads
+//      (L2 evict-first, no L1 allocation) and issues the 8 gathers v[col]
+//      back to back;
+//  (2) the thread walks the row ends inside its window with one fused
+//      multiply-add per nonzero, the row structure read from a window word
+//      computed once with the schedule (row-end mask, first row, "continues
+//      a row" bit): rows that end there are finished at once, the first one
+//      with a carry-in if it began in an earlier window, and the row still
+//      open at the window's end is carried out;
 //  (3) carries are combined by a segmented scan over threads (warp shuffles,
 //      then across warps in shared memory), so every thread does the same
 //      amount of work whatever the row lengths;
