@@ -312,10 +312,11 @@ static void enqueue_chunk_any(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
 
 // Iteration schedules: every candidate is timed with the real fused primal
 // (rows of A~^T) or dual (rows of A~) kernel on the initial state; the state
-// is zeroed again afterwards.  e > 0: segmented kernel with e nonzeros per
-// thread; e < 0: vector kernel with -e lanes per row (only if all rows are
-// short).  E = 8 is kept unless another choice is more than 5% faster, so
-// timing noise does not flip the schedule from one context to the next.
+// is zeroed again afterwards.  Candidates: the segmented kernel with 8, 16
+// or 32 nonzeros per thread (a vector kernel with -e lanes per row, e < 0,
+// only when options.tile_nnz asks for it and all rows are short).  E = 8 is
+// kept unless another choice is more than 5% faster, so timing noise does not
+// flip the schedule from one context to the next.
 template <typename T>
 static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out) {
   const IterBuffers<T> B = iter_buffers<T>(ctx);
