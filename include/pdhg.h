@@ -97,6 +97,7 @@ void pdhg_default_options(pdhg_options* opt);
 /* Create a solver context for one LP (Section 2 standard form).
  *  m, n       rows and columns of A (m >= 1, n >= 1)
  *  row_ptr    int32[m+1], row_ptr[0] = 0, non-decreasing, nnz = row_ptr[m]
+ *             <= 2^31 - 2^16 (int32 tile indexing)
  *  col        int32[nnz], strictly increasing within each row, in [0, n)
  *  val        float64[nnz], finite
  *  b, c       float64[m], float64[n], finite

@@ -947,8 +947,9 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
         return PDHG_INVALID_ARG;
       }
       const int64_t g = nnz_off[l] + r[i + 1];
-      if (g >= (1LL << 31)) {
-        set_error("batch too large: total nonzeros must fit in int32");
+      if (g > kMaxNnz) {
+        set_error("batch too large: total nonzeros above %lld (int32 tile indexing)",
+                  (long long)kMaxNnz);
         return PDHG_INVALID_ARG;
       }
       ctx->h_a_rp[ctx->h_m_off[l] + i + 1] = (int32_t)g;

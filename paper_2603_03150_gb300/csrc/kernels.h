@@ -36,6 +36,10 @@ struct IterBuffers {
   int32_t m, n;
 };
 
+// Nonzeros a context accepts: tiles index nonzeros with int32 and a window may
+// reach 32 past the last one.
+constexpr int64_t kMaxNnz = (int64_t(1) << 31) - (int64_t(1) << 16);
+
 struct Launch {
   int grid;
   size_t smem;

@@ -702,6 +702,11 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
       return PDHG_INVALID_ARG;
     }
   ctx->nnz = ctx->h_a_rp[m];
+  if (ctx->nnz > kMaxNnz) {
+    set_error("nnz = %lld exceeds the limit %lld of the int32 tile indexing",
+              (long long)ctx->nnz, (long long)kMaxNnz);
+    return PDHG_INVALID_ARG;
+  }
 
   stage("row pointer checks");
   CKS(alloc_arrays(ctx));

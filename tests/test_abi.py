@@ -53,3 +53,23 @@ def test_default_options_without_gpu(libpath):
     pdhg.lib().pdhg_default_options(ctypes.byref(o))
     assert o.eval_freq == 64 and o.ruiz_iters == 10 and abs(o.eta_safety - 0.95) < 1e-15
     assert o.precision == 0 and o.use_graphs == 1
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/pdhg.h compiles as C99 (no C++ in the boundary) and every
+    declared entry point can be referenced from C."""
+    gcc = "gcc"
+    import shutil
+    import subprocess
+    if shutil.which(gcc) is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi_check.c"
+    refs = "\n".join(f"  (pdhg_fn)&{n}," for n in declared())
+    src.write_text('#include "pdhg.h"\n'
+                   "typedef void (*pdhg_fn)(void);\n"
+                   "pdhg_fn pdhg_abi_refs[] = {\n" + refs + "\n};\n"
+                   "int main(void) { pdhg_options o; pdhg_default_options(&o); return (int)o.eval_freq == 0; }\n")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-c", str(src),
+                        "-I", os.path.join(ROOT, "include"), "-o", str(tmp_path / "abi_check.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
