@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(BLOCK) k_cg_ATu(SchedView S, const int32_t* rp
     CgState& c = cg[l];
     if (c.done) continue;
     double s = 0.0;
+#pragma unroll 4  // independent record loads in flight together
     for (int t = lp_tiles[l]; t < lp_tiles[l + 1]; ++t) s += __ldcg(rec + t);
     c.pq = s;
     c.alpha = s > 0.0 ? c.rr / s : 0.0;
@@ -176,6 +177,7 @@ __global__ void k_cg_update(SchedView S, double* w, double* r, const double* p, 
     CgState& c = cg[l];
     if (c.done) continue;
     double s = 0.0;
+#pragma unroll 4  // independent record loads in flight together
     for (int t = lp_tiles[l]; t < lp_tiles[l + 1]; ++t) s += __ldcg(rec + t);
     c.beta = c.rr > 0.0 ? s / c.rr : 0.0;
     c.rr = s;
@@ -231,6 +233,7 @@ __global__ void k_cg_start_final(const double* rec2, const int32_t* lp_tiles, in
                                  CgState* cg, double tol, int max_iter) {
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
     double a = 0.0, b = 0.0;
+#pragma unroll 4  // independent record loads in flight together
     for (int t = lp_tiles[l]; t < lp_tiles[l + 1]; ++t) {
       a += rec2[2 * (size_t)t];
       b += rec2[2 * (size_t)t + 1];

@@ -205,9 +205,11 @@ __global__ void __launch_bounds__(BLOCK) k_beval(BatchBuffers<T> B, int chunk) {
     double tot[kEvalQ];
 #pragma unroll
     for (int k = 0; k < kEvalQ; ++k) tot[k] = 0.0;
+#pragma unroll 4  // independent record loads in flight together
     for (int t = B.lp_t_tiles[l]; t < B.lp_t_tiles[l + 1]; ++t)
 #pragma unroll
       for (int k = 0; k < kEvalQ; ++k) tot[k] += __ldcg(B.rec_t + (size_t)t * kEvalQ + k);
+#pragma unroll 4  // independent record loads in flight together
     for (int t = B.lp_a_tiles[l]; t < B.lp_a_tiles[l + 1]; ++t)
 #pragma unroll
       for (int k = 0; k < kEvalQ; ++k) tot[k] += __ldcg(B.rec_a + (size_t)t * kEvalQ + k);
@@ -332,6 +334,7 @@ __global__ void __launch_bounds__(BLOCK) k_bpow_ATu(SchedView S, const int32_t* 
     PowerState& p = ps[l];
     if (p.stopped) continue;
     double lam = 0.0, nw2 = 0.0;
+#pragma unroll 4  // independent record loads in flight together
     for (int t = lp_tiles[l]; t < lp_tiles[l + 1]; ++t) {
       lam += __ldcg(rec + (size_t)t * kRecP);
       nw2 += __ldcg(rec + (size_t)t * kRecP + 1);
@@ -612,6 +615,7 @@ __global__ void k_bws_mu(const double* rec, const int32_t* lp_tiles, const int64
                          int count, double mu_min, double* mu) {
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
     double s = 0.0;
+#pragma unroll 4  // independent record loads in flight together
     for (int t = lp_tiles[l]; t < lp_tiles[l + 1]; ++t) s += rec[t];
     mu[l] = fmax(s / (double)(n_off[l + 1] - n_off[l]), mu_min);
   }
