@@ -36,6 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 WORKLOADS = {
     "powerlaw": ("planted LP m=200000 n=1000000 nnz=5000000, power-law row lengths "
                  "(exponent 2.1, 4..20000), 1% of rows x1e3, CSR int32, seed 0"),
+    "powerlaw50m": ("planted LP m=2000000 n=10000000 nnz=50000000, power-law row lengths "
+                    "(exponent 2.1, 4..20000), 1% of rows x1e3, CSR int32, seed 0"),
     "transport": ("balanced transportation LP 2000 supply x 2000 demand, m=4000 "
                   "n=4000000 nnz=8000000, seed 0"),
     "small": "planted LP m=200 n=500, 5 nnz per column, seed 0",
@@ -62,6 +64,8 @@ def make_lp(name):
     from paper_2603_03150_gb300 import lpgen
     if name == "powerlaw":
         return lpgen.powerlaw_lp()
+    if name == "powerlaw50m":
+        return lpgen.powerlaw_lp(m=2_000_000, n=10_000_000, nnz=50_000_000)
     if name == "transport":
         return lpgen.transportation_lp()
     return lpgen.planted_lp(200, 500, seed=0)
