@@ -323,6 +323,18 @@ def run_ours(args):
                           "mean_launch_ms": round(dm if dom == "primal" else pm, 5),
                           "achieved_gbs": round(ab["dual" if dom == "primal" else "primal"] /
                                                 (max(dm if dom == "primal" else pm, 1e-9) / 1e3) / 1e9, 1)}}
+    # the second bound: the same nonzeros' loads and random gathers without the
+    # row logic (pdhg_gather_floor), timed on a fresh context after the steps
+    with torch.cuda.stream(stream):
+        sf = pdhg.Solver(m, n, devt["row_ptr"], devt["col"], devt["val"], devt["b"], devt["c"],
+                         precision=args.precision, device_io=True, stream=stream.cuda_stream)
+        gf = {"dual": sf.gather_floor(True, 20), "primal": sf.gather_floor(False, 20)}
+        sf.close()
+    roofline["gather_floor"] = {
+        "what": "mean ms of a pass over the same nonzeros keeping only the index/value loads, "
+                "the random gathers and one FMA each (no row logic, scan or epilogue)",
+        "dual_ms": round(gf["dual"], 5), "primal_ms": round(gf["primal"], 5),
+        "frac": round(gf[dom] / dur, 4) if dur > 0 else None}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -275,6 +275,15 @@ pdhg_status pdhg_centered_point_noalloc(int32_t n, const double* x, const double
  * every kernel node).  */
 pdhg_status pdhg_get_launch_count(pdhg_ctx* ctx, int64_t* launches);
 
+/* Diagnostic (the paper has no counterpart): mean time in ms of `reps` launches
+ * of a pass over the same nonzeros as the dual (on_a = 1: A~, gathering x) or
+ * primal (on_a = 0: A~^T, gathering y) kernel that keeps only the memory work -
+ * 128-bit loads of column indices and values with the same cache policy, the
+ * random gathers and one multiply-add each - and no row logic, scan or
+ * epilogue: the gather-rate floor the SpMV kernels are measured against.
+ * Single-LP contexts; leaves the solver state unchanged.  */
+pdhg_status pdhg_gather_floor(pdhg_ctx* ctx, int32_t on_a, int32_t reps, double* ms);
+
 void pdhg_destroy(pdhg_ctx* ctx);
 
 /* Message for the last failing call on this thread ("" if none). */

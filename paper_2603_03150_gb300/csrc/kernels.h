@@ -148,6 +148,10 @@ void launch_pow_norm(int n, const double* w, double* v, PowerState* ps, cudaStre
 void launch_init_scalars(Scalars* sc, const double* sums, const PowerState* ps,
                          double eta_safety, cudaStream_t s);
 cudaError_t configure_setup_kernels(size_t max_smem);
+// gather-rate floor pass (diagnostic): nnz nonzeros in groups of 8
+template <typename T>
+void launch_gather_floor(const int32_t* col, const T* val, const T* v, int64_t nnz, T* sink,
+                         int grid, cudaStream_t s);
 cudaError_t configure_tile_kernels(size_t max_smem);
 int tile_occupancy(int which, int e, size_t smem);
 

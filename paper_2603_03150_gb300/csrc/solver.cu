@@ -1284,6 +1284,45 @@ extern "C" pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int
   return PDHG_OK;
 }
 
+extern "C" pdhg_status pdhg_gather_floor(pdhg_ctx* ctx, int32_t on_a, int32_t reps, double* ms) {
+  g_last_error.clear();
+  if (!ctx || !ms || reps < 1) {
+    set_error("need ctx, ms and reps >= 1");
+    return PDHG_INVALID_ARG;
+  }
+  if (ctx->batch) {
+    set_error("this entry point takes a single-LP context");
+    return PDHG_INVALID_ARG;
+  }
+  const int32_t* col = on_a ? ctx->a_col : ctx->t_col;
+  const void* val = ctx->mixed ? (const void*)(on_a ? ctx->a_val32 : ctx->t_val32)
+                               : (const void*)(on_a ? ctx->a_val64 : ctx->t_val64);
+  const void* v = on_a ? ctx->x : ctx->y;  // the gathered vector of that half-step
+  const int grid = ctx->nsm * 8;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int it = 0; it < reps + 2; ++it) {
+    if (it == 2) CK(cudaEventRecord(e0, ctx->stream));
+    if (ctx->mixed)
+      launch_gather_floor<float>(col, (const float*)val, (const float*)v, ctx->nnz,
+                                 (float*)ctx->out_m1, grid, ctx->stream);
+    else
+      launch_gather_floor<double>(col, (const double*)val, (const double*)v, ctx->nnz,
+                                  (double*)ctx->out_m1, grid, ctx->stream);
+  }
+  ctx->launches += reps + 2;
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, ctx->stream));
+  CK(cudaEventSynchronize(e1));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = (double)t / reps;
+  return PDHG_OK;
+}
+
 extern "C" pdhg_status pdhg_get_launch_count(pdhg_ctx* ctx, int64_t* launches) {
   g_last_error.clear();
   if (!ctx || !launches) {

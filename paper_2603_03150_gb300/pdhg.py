@@ -85,6 +85,7 @@ _SIGS = {
     "pdhg_get_kernel_timing": (_I32, [_P, _P, _P, _P]),
     "pdhg_get_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pdhg_get_launch_count": (_I32, [_P, _P]),
+    "pdhg_gather_floor": (_I32, [_P, _I32, _I32, _P]),
     "pdhg_batch_create": (_I32, [_PP, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
     "pdhg_batch_solve": (_I32, [_P, _D, _I64, _P]),
     "pdhg_batch_get": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -315,6 +316,12 @@ class Solver:
         keys = ["a_tile_nnz", "a_block", "a_tiles", "at_tile_nnz", "at_block", "at_tiles",
                 "a_variant", "at_variant"]
         return {k: x.value for k, x in zip(keys, v)}
+
+    def gather_floor(self, on_a: bool, reps: int = 10) -> float:
+        """Mean ms of the row-logic-free gather pass over A~ (on_a) or A~^T."""
+        ms = _D()
+        _check(self._L.pdhg_gather_floor(self._ctx, 1 if on_a else 0, reps, ctypes.byref(ms)))
+        return ms.value
 
     def launch_count(self) -> int:
         v = _I64()

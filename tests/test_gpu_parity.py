@@ -407,3 +407,15 @@ def test_lp_without_optimum_ends_cleanly(kind, precision):
         st2 = s.solve(1e-6, 3200)
         assert st2 in (pdhg.PDHG_MAX_ITER, pdhg.PDHG_NUMERICAL_ERROR)
         assert s.info(violation=False)["iters"] <= 3200
+
+
+def test_gather_floor_diagnostic_runs_and_leaves_state():
+    lp = heavy_row_lp(0)
+    with pdhg.Solver.from_lp(lp, precision="fp32") as s:
+        s.solve(1e-12, 64)
+        before = s.state()
+        t_a, t_t = s.gather_floor(True, 3), s.gather_floor(False, 3)
+        assert t_a > 0 and t_t > 0
+        after = s.state()
+        for k in ["x", "y", "x_avg", "y_avg"]:
+            np.testing.assert_array_equal(before[k], after[k])
