@@ -89,6 +89,20 @@ typedef struct pdhg_options {
                               evaluation's second candidate is T(z) (single-LP
                               contexts only)                                   */
   double reflection;       /* rho of method 1, in [0, 1] (default 1)           */
+  int32_t spmv_layout;     /* FP32_MIXED single-LP half-steps (the products
+                              A~^T y and A~ x+ of Section 2's iteration):
+                              0 (default): per matrix, the faster of the CSR
+                              tiles and the column panels, timed at create
+                              when autotune is on (CSR tiles otherwise);
+                              1: CSR tiles only; 2: column panels wherever
+                              they apply.  Column panels stage a slice of the
+                              gathered vector in shared memory and apply when
+                              (panels x rows) <= 2 nnz + rows and nnz <= 2^30;
+                              float64 and batched contexts use CSR tiles.  */
+  int32_t panel_width;     /* 0 (default): the widest panel shared memory holds
+                              (about 49k columns); > 0: at most this many
+                              columns per panel (rounded down to a multiple of
+                              8, at least 8)                                   */
 } pdhg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -170,10 +184,18 @@ pdhg_status pdhg_get_log(pdhg_ctx* ctx, int32_t cap, int32_t* count, int64_t* k,
                          int32_t* flags, double* kkt);
 
 /* With options.kernel_timing = 1: mean duration (ms) of the sampled primal
- * (A^T y + projection) and dual (A x + dual step) kernel launches of the last
- * pdhg_solve, and the number of samples of each.  */
+ * (A^T y + projection) and dual (A x + dual step) half-steps of the last
+ * pdhg_solve (one kernel on the CSR tiles, two on the column panels), and
+ * the number of samples of each.  */
 pdhg_status pdhg_get_kernel_timing(pdhg_ctx* ctx, double* primal_ms, double* dual_ms,
                                    int64_t* samples);
+
+/* With options.kernel_timing = 1: the same samples split by kernel, ms[4]
+ * (HOST) = {primal SpMV kernel, primal row pass, dual SpMV kernel, dual row
+ * pass}.  A half-step on the CSR tiles is one fused kernel (its row pass
+ * reads 0); on the column panels, the panel SpMV and the row pass that adds
+ * the panel sums and applies the step.  */
+pdhg_status pdhg_get_kernel_timing_parts(pdhg_ctx* ctx, double* ms, int64_t* samples);
 
 /* Tile schedule picked for A (dual kernel) and A^T (primal kernel): nonzeros
  * per tile (at most), threads per block, tiles, and the SpMV variant (8, 16,
@@ -182,6 +204,14 @@ pdhg_status pdhg_get_kernel_timing(pdhg_ctx* ctx, double* primal_ms, double* dua
 pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int32_t* a_block,
                               int32_t* a_tiles, int32_t* at_tile_nnz, int32_t* at_block,
                               int32_t* at_tiles, int32_t* a_variant, int32_t* at_variant);
+
+/* Column-panel layout of A (dual half-step) and A^T (primal half-step): the
+ * number of panels (0: that half-step runs on the CSR tiles), the panel
+ * width in columns, the pseudo-rows (a row's nonzeros inside one panel) and
+ * the warp tiles.  Any pointer may be NULL; arrays are HOST int64[2] in the
+ * order {A, A^T}.  */
+pdhg_status pdhg_get_layout(pdhg_ctx* ctx, int64_t* panels, int64_t* panel_width,
+                            int64_t* pseudo_rows, int64_t* tiles);
 
 /* ---- batched solves -------------------------------------------------------
  * `count` independent LPs iterated together as one block-diagonal system: each

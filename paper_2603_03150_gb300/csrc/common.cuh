@@ -46,6 +46,43 @@ struct SchedView {
 };
 
 // ---------------------------------------------------------------------------
+// Column-panel layout of one matrix (float32 iterations).  The columns are cut
+// into panels of P; the nonzeros of row i inside panel p form pseudo-row
+// (p, i).  Pseudo-rows are ordered by (panel, row) and packed whole into warp
+// tiles of at most kPanelCap nonzeros, padded with zeros to a multiple of 8;
+// a pseudo-row longer than kPanelCap is a tile of its own (nps < 0).  Each
+// block stages one panel of the gathered vector in shared memory and runs a
+// contiguous range of that panel's tiles; each pseudo-row's sum goes to
+// partial[p * rows + i] (entries of empty pseudo-rows stay zero).
+// ---------------------------------------------------------------------------
+constexpr int kPanelWarps = 32;                 // warps of a panel block
+constexpr int kPanelCap = 256;                  // nonzeros of a warp tile
+constexpr int kPanelStage = kPanelWarps * kPanelCap;  // staged sums per block (floats)
+constexpr int kPanelDescCache = 256;            // tile descriptors a block keeps in shared memory
+
+struct PanelTile {
+  int32_t nz_begin;  // first nonzero (a multiple of 8)
+  int32_t nz_len;    // nonzeros incl. padding (a multiple of 8)
+  int32_t ps_begin;  // first pseudo-row
+  int32_t nps;       // pseudo-rows; -1: one pseudo-row longer than kPanelCap
+};
+
+struct PanelBlock {
+  int32_t panel, t_begin, t_end, pad;
+};
+
+struct PanelView {
+  const PanelTile* tiles;
+  const PanelBlock* blocks;
+  const float* val;     // [nonzeros incl. padding]
+  const uint16_t* col;  // column within the panel
+  const uint32_t* wd;   // window words, one per 8 nonzeros
+  const int32_t* psrow; // row of each pseudo-row
+  float* partial;       // [npanels][rows]
+  int32_t P, npanels, rows, cols, nblocks, ntiles;
+};
+
+// ---------------------------------------------------------------------------
 // Device-resident solver scalars (float64 state of the restart rule).
 // ---------------------------------------------------------------------------
 enum { Q_S1 = 0,  // ||b~ - A~x||^2            (scaled primal residual)

@@ -62,11 +62,26 @@ struct DevSched {
   SchedView view{};
 };
 
+// column-panel layout of one matrix (float32 single-LP iterations)
+struct DevPanel {
+  PanelTile* tiles = nullptr;
+  PanelBlock* blocks = nullptr;
+  float* val = nullptr;
+  uint16_t* col = nullptr;
+  uint32_t* wd = nullptr;
+  int32_t* psrow = nullptr;
+  float* partial = nullptr;
+  PanelView view{};
+  int64_t pseudo_rows = 0, nnz_padded = 0;
+  bool on = false;  // the half-step over this matrix runs on the panels
+};
+
 }  // namespace pdhg
 
 struct pdhg_ctx;
 void pdhg_free_adjoint(pdhg_ctx* ctx);
 
+using pdhg::DevPanel;
 using pdhg::DevSched;
 using pdhg::Launch;
 using pdhg::PowerState;
@@ -119,14 +134,18 @@ struct pdhg_ctx {
   // schedules and launch shapes
   DevSched sa, st;      // iteration schedules (autotuned nonzeros per thread)
   DevSched sa8, st8;    // float64 report / Algorithm 1 / power iteration
+  DevPanel pa, pt;      // column panels of A~ (dual) and A~^T (primal), when chosen
+  int panel_row_grid_a = 1, panel_row_grid_t = 1;
   Launch l_prim{}, l_dual{}, l_eval{}, l_a64{}, l_t64{};
   int restart_grid = 1;
   // graphs and polling
   cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
   cudaEvent_t ev_done[2] = {nullptr, nullptr};
-  cudaEvent_t ev_k[2][4] = {};
+  // sampled iteration: before / between the two kernels / after the primal
+  // half-step, then the same for the dual (CSR tiles: one kernel, nothing between)
+  cudaEvent_t ev_k[2][6] = {};
   Scalars* h_sc[2] = {nullptr, nullptr};
-  double timing_sum[2] = {0, 0};
+  double timing_sum[4] = {0, 0, 0, 0};  // primal kernel 1, 2, dual kernel 1, 2
   long long timing_n = 0;
   // cached host data
   double omega0 = 1.0;
@@ -184,5 +203,10 @@ pdhg_status upload_lp(pdhg_ctx* ctx, const int32_t* col, const double* val, cons
                       const double* c);
 pdhg_status prepare_matrix(pdhg_ctx* ctx);
 pdhg_status polling_resources(pdhg_ctx* ctx);
+// column panels (panel.cu): the panel width and count for the rows of A~
+// (on_a) or A~^T, false where the panels do not apply (float64, batches, or
+// dense partial sums above about twice the nonzeros); the device layout
+bool panel_shape(const pdhg_ctx* ctx, bool on_a, int* P, int* npanels);
+pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out);
 
 }  // namespace pdhg

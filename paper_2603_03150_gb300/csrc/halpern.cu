@@ -12,25 +12,12 @@
 // cache A~x <- lam((1+rho) h - rho A~x) + (1-lam) A~x0 by linearity.
 // The evaluation then sees (x, y) and T(z) = (x^, y^) as its two candidates.
 #include "dispatch.cuh"
+#include "epilogues.cuh"
 #include "kernels.h"
 #include "spmv_tile.cuh"
 
 namespace pdhg {
 
-template <typename T>
-struct HalpernPrimalEpi {
-  T* __restrict__ x;
-  T* __restrict__ x_hat;
-  const T* __restrict__ c;
-  const T* __restrict__ x0;
-  T tau, lam, rho;
-  __device__ __forceinline__ void row(int j, const T (&s)[1], int) {
-    const T xo = x[j];
-    const T xh = fmax(T(0), xo - tau * (c[j] - s[0]));
-    x_hat[j] = xh;
-    x[j] = lam * ((T(1) + rho) * xh - rho * xo) + (T(1) - lam) * x0[j];
-  }
-};
 
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_hprimal(IterBuffers<T> B, int i) {
@@ -44,26 +31,6 @@ __global__ void __launch_bounds__(BLOCK) k_hprimal(IterBuffers<T> B, int i) {
   run_sched<T, 1, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
 }
 
-template <typename T>
-struct HalpernDualEpi {
-  T* __restrict__ y;
-  const T* __restrict__ b;
-  T* __restrict__ Ax;
-  T* __restrict__ y_hat;
-  T* __restrict__ Ax_hat;
-  const T* __restrict__ y0;
-  const T* __restrict__ Ax0;
-  T sigma, lam, rho;
-  __device__ __forceinline__ void row(int i, const T (&s)[1], int) {
-    const T h = s[0];
-    const T yo = y[i], axo = Ax[i];
-    const T yh = yo + sigma * (b[i] - (h + h) + axo);
-    y_hat[i] = yh;
-    Ax_hat[i] = h;
-    y[i] = lam * ((T(1) + rho) * yh - rho * yo) + (T(1) - lam) * y0[i];
-    Ax[i] = lam * ((T(1) + rho) * h - rho * axo) + (T(1) - lam) * Ax0[i];
-  }
-};
 
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_hdual(IterBuffers<T> B, int i) {

@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include "dispatch.cuh"
+#include "epilogues.cuh"
 #include "eval_rule.cuh"
 #include "kernels.h"
 #include "spmv_tile.cuh"
@@ -14,19 +15,6 @@ namespace pdhg {
 // ---------------------------------------------------------------------------
 // K1: x+ = max(0, x - tau (c~ - A~^T y)), running average of x.
 // ---------------------------------------------------------------------------
-template <typename T>
-struct PrimalEpi {
-  T* __restrict__ x;
-  const T* __restrict__ c;
-  T* __restrict__ x_avg;
-  T tau, w;
-  bool first;
-  __device__ __forceinline__ void row(int j, const T (&s)[1], int) {
-    const T xn = fmax(T(0), x[j] - tau * (c[j] - s[0]));
-    x[j] = xn;
-    x_avg[j] = first ? xn : x_avg[j] + (xn - x_avg[j]) * w;
-  }
-};
 
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_primal(IterBuffers<T> B, int i) {
@@ -43,24 +31,6 @@ __global__ void __launch_bounds__(BLOCK) k_primal(IterBuffers<T> B, int i) {
 // K2: h = A~ x+;  y+ = y + sigma (b~ - 2h + A~x)   (= b~ - A~(2x+ - x));
 // caches A~x+ and the running averages of y and A~x.
 // ---------------------------------------------------------------------------
-template <typename T>
-struct DualEpi {
-  T* __restrict__ y;
-  const T* __restrict__ b;
-  T* __restrict__ Ax;
-  T* __restrict__ y_avg;
-  T* __restrict__ Ax_avg;
-  T sigma, w;
-  bool first;
-  __device__ __forceinline__ void row(int i, const T (&s)[1], int) {
-    const T h = s[0];
-    const T yn = y[i] + sigma * (b[i] - (h + h) + Ax[i]);
-    Ax[i] = h;
-    y[i] = yn;
-    y_avg[i] = first ? yn : y_avg[i] + (yn - y_avg[i]) * w;
-    Ax_avg[i] = first ? h : Ax_avg[i] + (h - Ax_avg[i]) * w;
-  }
-};
 
 template <typename T, int BLOCK, int E>
 __global__ void __launch_bounds__(BLOCK) k_dual(IterBuffers<T> B, int i) {

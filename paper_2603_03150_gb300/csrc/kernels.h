@@ -153,6 +153,16 @@ template <typename T>
 void launch_gather_floor(const int32_t* col, const T* val, const T* v, int64_t nnz, T* sink,
                          int grid, cudaStream_t s);
 cudaError_t configure_tile_kernels(size_t max_smem);
+// column-panel half-steps (panel.cu, float32): the panel SpMV then the row
+// pass with the primal (dual = false) or dual epilogue of the method
+// (0 averaged, 1 Halpern); row_grid blocks of 256 threads for the row pass;
+// `between` (optional) is recorded between the two kernels
+void launch_panel_half(const IterBuffers<float>& B, const PanelView& V, bool dual, int method,
+                       int row_grid, int i, cudaStream_t s, cudaEvent_t between = nullptr);
+size_t panel_smem(int P);
+// blocks of 256 threads for the row pass over `rows` rows of `npanels` panels
+int panel_row_grid(int rows, int npanels, int nsm);
+cudaError_t configure_panel_kernels(size_t max_smem);
 int tile_occupancy(int which, int e, size_t smem);
 
 // ---- reflected Halpern half-steps (halpern.cu) ----------------------------

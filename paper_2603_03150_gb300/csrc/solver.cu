@@ -266,38 +266,61 @@ static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
   return B;
 }
 
-// the iteration's half-steps for the configured method
+// the iteration's half-steps for the configured method and layout (column
+// panels: two kernels; CSR tiles: one fused kernel)
+// `between` (optional): an event recorded between the half-step's kernels
+// (right after the fused kernel of the CSR tiles)
 template <typename T>
-static void launch_prim_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i) {
+static void launch_prim_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i,
+                             cudaEvent_t between = nullptr) {
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->pt.on) {
+      launch_panel_half(B, ctx->pt.view, false, ctx->opt.method, ctx->panel_row_grid_t, i,
+                        ctx->stream, between);
+      return;
+    }
+  }
   if (ctx->opt.method == 1)
     launch_hprimal<T>(B, ctx->l_prim, i, ctx->stream);
   else
     launch_primal<T>(B, ctx->l_prim, i, ctx->stream);
+  if (between) cudaEventRecordWithFlags(between, ctx->stream, cudaEventRecordExternal);
 }
 template <typename T>
-static void launch_dual_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i) {
+static void launch_dual_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i,
+                             cudaEvent_t between = nullptr) {
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->pa.on) {
+      launch_panel_half(B, ctx->pa.view, true, ctx->opt.method, ctx->panel_row_grid_a, i,
+                        ctx->stream, between);
+      return;
+    }
+  }
   if (ctx->opt.method == 1)
     launch_hdual<T>(B, ctx->l_dual, i, ctx->stream);
   else
     launch_dual<T>(B, ctx->l_dual, i, ctx->stream);
+  if (between) cudaEventRecordWithFlags(between, ctx->stream, cudaEventRecordExternal);
 }
+static int prim_launches(const pdhg_ctx* ctx) { return ctx->pt.on ? 2 : 1; }
+static int dual_launches(const pdhg_ctx* ctx) { return ctx->pa.on ? 2 : 1; }
 
 // `len` iterations followed by the evaluation and the restart.  With
 // `timing`, events bracket the primal and dual kernels of iteration len/2.
 template <typename T>
 static void enqueue_chunk(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
   const IterBuffers<T> B = iter_buffers<T>(ctx);
-  ctx->launches += 2LL * len + 2;
+  ctx->launches += (long long)(prim_launches(ctx) + dual_launches(ctx)) * len + 2;
   for (int i = 0; i < len; ++i) {
     const bool sample = timing && i == len / 2;
     if (sample) cudaEventRecordWithFlags(timing[0], ctx->stream, cudaEventRecordExternal);
-    launch_prim_step<T>(ctx, B, i);
+    launch_prim_step<T>(ctx, B, i, sample ? timing[1] : nullptr);
     if (sample) {
-      cudaEventRecordWithFlags(timing[1], ctx->stream, cudaEventRecordExternal);
       cudaEventRecordWithFlags(timing[2], ctx->stream, cudaEventRecordExternal);
+      cudaEventRecordWithFlags(timing[3], ctx->stream, cudaEventRecordExternal);
     }
-    launch_dual_step<T>(ctx, B, i);
-    if (sample) cudaEventRecordWithFlags(timing[3], ctx->stream, cudaEventRecordExternal);
+    launch_dual_step<T>(ctx, B, i, sample ? timing[4] : nullptr);
+    if (sample) cudaEventRecordWithFlags(timing[5], ctx->stream, cudaEventRecordExternal);
   }
   launch_eval<T>(B, ctx->l_eval, len, ctx->stream);
   launch_restart<T>(B, ctx->restart_grid, ctx->stream);
@@ -324,13 +347,39 @@ static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const int warm = 3, reps = 10;
-  ctx->launches += warm + reps;
+  ctx->launches += (long long)(warm + reps) * (on_a ? dual_launches(ctx) : prim_launches(ctx));
   for (int it = 0; it < warm + reps; ++it) {
     if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
     if (on_a)
       launch_dual_step<T>(ctx, B, 0);
     else
       launch_prim_step<T>(ctx, B, 0);
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, ctx->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms / reps;
+  return PDHG_OK;
+}
+
+// mean time of one whole iteration (primal then dual half-step) over 10,
+// after 3 untimed
+template <typename T>
+static pdhg_status time_iterations(pdhg_ctx* ctx, float* ms_out) {
+  const IterBuffers<T> B = iter_buffers<T>(ctx);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int warm = 3, reps = 10;
+  ctx->launches += (long long)(warm + reps) * (prim_launches(ctx) + dual_launches(ctx));
+  for (int it = 0; it < warm + reps; ++it) {
+    if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
+    launch_prim_step<T>(ctx, B, 0);
+    launch_dual_step<T>(ctx, B, 0);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(e1, ctx->stream));
@@ -399,6 +448,49 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
       }
     }
     (on_a ? ctx->sa : ctx->st) = best;
+    if (on_a)
+      ctx->l_dual = make_launch(ctx, dual_kind(ctx), best.view.e,
+                                smem_for(0, mx, best.view.max_rows, best.view.e), best.view.ntiles);
+    else
+      ctx->l_prim = make_launch(ctx, prim_kind(ctx), best.view.e,
+                                smem_for(0, mx, best.view.max_rows, best.view.e), best.view.ntiles);
+
+    // column panels where they apply: forced (spmv_layout 2), or candidates
+    // timed below against the CSR tiles picked above (autotune on, tile_nnz 0)
+    const int lay = ctx->opt.spmv_layout;
+    int pw = 0, np = 0;
+    if ((lay == 2 || (lay == 0 && cands.size() > 1)) && panel_shape(ctx, on_a, &pw, &np)) {
+      DevPanel& dp = on_a ? ctx->pa : ctx->pt;
+      CKS(build_panel_layout(ctx, on_a, &dp));
+      const int rows = on_a ? ctx->m : ctx->n;
+      (on_a ? ctx->panel_row_grid_a : ctx->panel_row_grid_t) =
+          panel_row_grid(rows, dp.view.npanels, ctx->nsm);
+    }
+  }
+  // With panel candidates: whole iterations (both half-steps in turn, as the
+  // solve runs them, so each matrix streams from where the other left the
+  // L2) for every CSR / panel combination; the fastest is kept.
+  if (ctx->opt.spmv_layout == 0 && (ctx->pa.on || ctx->pt.on)) {
+    const bool ca = ctx->pa.on, ct = ctx->pt.on;
+    float best = 1e30f;
+    int best_combo = 0;
+    for (int combo = 0; combo < 4; ++combo) {
+      const bool ua = combo & 1, ut = (combo >> 1) & 1;
+      if ((ua && !ca) || (ut && !ct)) continue;
+      ctx->pa.on = ua;
+      ctx->pt.on = ut;
+      float ms = 0.f;
+      CKS(time_iterations<float>(ctx, &ms));
+      if (ctx->opt.verbose)
+        std::fprintf(stderr, "pdhg_create: tune iteration A %s, A^T %s: %8.4f ms\n",
+                     ua ? "panels" : "CSR   ", ut ? "panels" : "CSR   ", ms);
+      if (ms < best) {
+        best = ms;
+        best_combo = combo;
+      }
+    }
+    ctx->pa.on = (best_combo & 1) != 0;
+    ctx->pt.on = ((best_combo >> 1) & 1) != 0;
   }
   const SchedView &A = ctx->sa.view, &T = ctx->st.view;
   ctx->l_prim = make_launch(ctx, prim_kind(ctx), T.e, smem_for(0, mx, T.max_rows, T.e), T.ntiles);
@@ -469,6 +561,8 @@ extern "C" void pdhg_default_options(pdhg_options* o) {
   o->verbose = 0;
   o->method = 0;
   o->reflection = 1.0;
+  o->spmv_layout = 0;
+  o->panel_width = 0;
 }
 
 // device attributes, stream, kernel shared-memory limits
@@ -487,6 +581,7 @@ pdhg_status pdhg::setup_device(pdhg_ctx* ctx) {
   }
   CK(configure_tile_kernels(ctx->smem_optin));
   CK(configure_halpern_kernels(ctx->smem_optin));
+  CK(configure_panel_kernels(ctx->smem_optin));
   CK(configure_setup_kernels(ctx->smem_optin));
 
   return PDHG_OK;
@@ -786,7 +881,7 @@ pdhg_status pdhg::polling_resources(pdhg_ctx* ctx) {
   for (int g = 0; g < 2; ++g) {
     CK(cudaEventCreateWithFlags(&ctx->ev_done[g], cudaEventDisableTiming));
     CK(cudaMallocHost((void**)&ctx->h_sc[g], sizeof(Scalars)));
-    for (int e = 0; e < 4; ++e) CK(cudaEventCreate(&ctx->ev_k[g][e]));
+    for (int e = 0; e < 6; ++e) CK(cudaEventCreate(&ctx->ev_k[g][e]));
   }
   CK(cudaGetLastError());
   return PDHG_OK;
@@ -818,9 +913,11 @@ extern "C" pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const i
       (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED) ||
       ctx->opt.tile_nnz < -8 || ctx->opt.tile_nnz > 8192 ||
       (ctx->opt.method != 0 && ctx->opt.method != 1) ||
-      !(ctx->opt.reflection >= 0.0 && ctx->opt.reflection <= 1.0)) {
+      !(ctx->opt.reflection >= 0.0 && ctx->opt.reflection <= 1.0) ||
+      ctx->opt.spmv_layout < 0 || ctx->opt.spmv_layout > 2 || ctx->opt.panel_width < 0) {
     set_error("invalid options (eval_freq >= 1, ruiz_iters >= 0, precision 0/1, "
-              "-8 <= tile_nnz <= 8192, method 0/1, 0 <= reflection <= 1)");
+              "-8 <= tile_nnz <= 8192, method 0/1, 0 <= reflection <= 1, spmv_layout 0..2, "
+              "panel_width >= 0)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }
@@ -849,7 +946,7 @@ extern "C" void pdhg_destroy(pdhg_ctx* ctx) {
     if (ctx->chunk_exec[g]) cudaGraphExecDestroy(ctx->chunk_exec[g]);
     if (ctx->ev_done[g]) cudaEventDestroy(ctx->ev_done[g]);
     if (ctx->h_sc[g]) cudaFreeHost(ctx->h_sc[g]);
-    for (int e = 0; e < 4; ++e)
+    for (int e = 0; e < 6; ++e)
       if (ctx->ev_k[g][e]) cudaEventDestroy(ctx->ev_k[g][e]);
   }
   pdhg_free_adjoint(ctx);
@@ -892,7 +989,7 @@ extern "C" pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_ite
   hs.ticket = 0;
   CK(cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
   if (ctx->opt.use_graphs) CKS(build_graphs(ctx));
-  ctx->timing_sum[0] = ctx->timing_sum[1] = 0.0;
+  for (double& v : ctx->timing_sum) v = 0.0;
   ctx->timing_n = 0;
 
   // Chunks are issued one ahead: after issuing chunk j the host waits for
@@ -907,11 +1004,12 @@ extern "C" pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_ite
     pending[sl] = false;
     const Scalars* h = ctx->h_sc[sl];
     if (sampled[sl] && h->k == expect_k[sl]) {
-      float a = 0.f, d = 0.f;
-      CK(cudaEventElapsedTime(&a, ctx->ev_k[sl][0], ctx->ev_k[sl][1]));
-      CK(cudaEventElapsedTime(&d, ctx->ev_k[sl][2], ctx->ev_k[sl][3]));
-      ctx->timing_sum[0] += a;
-      ctx->timing_sum[1] += d;
+      float t[4] = {0.f, 0.f, 0.f, 0.f};
+      CK(cudaEventElapsedTime(&t[0], ctx->ev_k[sl][0], ctx->ev_k[sl][1]));
+      CK(cudaEventElapsedTime(&t[1], ctx->ev_k[sl][1], ctx->ev_k[sl][2]));
+      CK(cudaEventElapsedTime(&t[2], ctx->ev_k[sl][3], ctx->ev_k[sl][4]));
+      CK(cudaEventElapsedTime(&t[3], ctx->ev_k[sl][4], ctx->ev_k[sl][5]));
+      for (int q = 0; q < 4; ++q) ctx->timing_sum[q] += t[q];
       ctx->timing_n += 1;
     }
     sampled[sl] = false;
@@ -1258,8 +1356,20 @@ extern "C" pdhg_status pdhg_get_kernel_timing(pdhg_ctx* ctx, double* primal_ms, 
     return PDHG_INVALID_ARG;
   }
   const double nn = ctx->timing_n > 0 ? (double)ctx->timing_n : 1.0;
-  if (primal_ms) *primal_ms = ctx->timing_sum[0] / nn;
-  if (dual_ms) *dual_ms = ctx->timing_sum[1] / nn;
+  if (primal_ms) *primal_ms = (ctx->timing_sum[0] + ctx->timing_sum[1]) / nn;
+  if (dual_ms) *dual_ms = (ctx->timing_sum[2] + ctx->timing_sum[3]) / nn;
+  if (samples) *samples = ctx->timing_n;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_kernel_timing_parts(pdhg_ctx* ctx, double* ms, int64_t* samples) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  const double nn = ctx->timing_n > 0 ? (double)ctx->timing_n : 1.0;
+  if (ms)
+    for (int q = 0; q < 4; ++q) ms[q] = ctx->timing_sum[q] / nn;
   if (samples) *samples = ctx->timing_n;
   return PDHG_OK;
 }
@@ -1281,6 +1391,23 @@ extern "C" pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int
   if (at_tiles) *at_tiles = ctx->st.view.ntiles;
   if (a_variant) *a_variant = ctx->sa.view.e;
   if (at_variant) *at_variant = ctx->st.view.e;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_layout(pdhg_ctx* ctx, int64_t* panels, int64_t* panel_width,
+                                       int64_t* pseudo_rows, int64_t* tiles) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  const DevPanel* d[2] = {&ctx->pa, &ctx->pt};
+  for (int k = 0; k < 2; ++k) {
+    const bool on = d[k]->on;
+    if (panels) panels[k] = on ? d[k]->view.npanels : 0;
+    if (panel_width) panel_width[k] = on ? d[k]->view.P : 0;
+    if (pseudo_rows) pseudo_rows[k] = on ? d[k]->pseudo_rows : 0;
+    if (tiles) tiles[k] = on ? d[k]->view.ntiles : 0;
+  }
   return PDHG_OK;
 }
 

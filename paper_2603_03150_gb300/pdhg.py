@@ -54,6 +54,8 @@ class Options(ctypes.Structure):
         ("verbose", ctypes.c_int32),
         ("method", ctypes.c_int32),
         ("reflection", ctypes.c_double),
+        ("spmv_layout", ctypes.c_int32),
+        ("panel_width", ctypes.c_int32),
     ]
 
 
@@ -84,6 +86,8 @@ _SIGS = {
     "pdhg_get_log": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "pdhg_get_kernel_timing": (_I32, [_P, _P, _P, _P]),
     "pdhg_get_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "pdhg_get_layout": (_I32, [_P, _P, _P, _P, _P]),
+    "pdhg_get_kernel_timing_parts": (_I32, [_P, _P, _P]),
     "pdhg_get_launch_count": (_I32, [_P, _P]),
     "pdhg_gather_floor": (_I32, [_P, _I32, _I32, _P]),
     "pdhg_batch_create": (_I32, [_PP, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
@@ -168,7 +172,8 @@ class Solver:
                  power_rel_tol: float = 1e-10, device_io: bool = False, stream=None,
                  use_graphs: bool = True, autotune: bool = True, tile_nnz: int = 0,
                  kernel_timing: bool = False, method: str = "averaged",
-                 reflection: float = 1.0, verbose: bool = False):
+                 reflection: float = 1.0, spmv_layout: str = "auto", panel_width: int = 0,
+                 verbose: bool = False):
         L = lib()
         o = Options()
         L.pdhg_default_options(ctypes.byref(o))
@@ -189,6 +194,11 @@ class Solver:
             raise ValueError("method must be 'averaged' or 'halpern'")
         o.method = 1 if method == "halpern" else 0
         o.reflection = reflection
+        layouts = {"auto": 0, "csr": 1, "panels": 2}
+        if spmv_layout not in layouts:
+            raise ValueError("spmv_layout must be 'auto', 'csr' or 'panels'")
+        o.spmv_layout = layouts[spmv_layout]
+        o.panel_width = panel_width
         o.verbose = 1 if verbose else 0
         self.m, self.n = int(m), int(n)
         self.device_io = device_io
@@ -310,12 +320,29 @@ class Solver:
                                               ctypes.byref(s)))
         return dict(primal_ms=a.value, dual_ms=d.value, samples=s.value)
 
+    def kernel_timing_parts(self):
+        """Per kernel: primal SpMV (or fused), primal row pass, dual SpMV (or
+        fused), dual row pass (ms; 0 for a fused half-step's row pass)."""
+        ms = (ctypes.c_double * 4)()
+        s = _I64()
+        _check(self._L.pdhg_get_kernel_timing_parts(self._ctx, ms, ctypes.byref(s)))
+        return dict(primal_spmv_ms=ms[0], primal_rows_ms=ms[1], dual_spmv_ms=ms[2],
+                    dual_rows_ms=ms[3], samples=s.value)
+
     def schedule(self):
         v = [_I32() for _ in range(8)]
         _check(self._L.pdhg_get_schedule(self._ctx, *[ctypes.byref(x) for x in v]))
         keys = ["a_tile_nnz", "a_block", "a_tiles", "at_tile_nnz", "at_block", "at_tiles",
                 "a_variant", "at_variant"]
         return {k: x.value for k, x in zip(keys, v)}
+
+    def layout(self):
+        """Column-panel layout per half-step: {"a": {...}, "at": {...}} with the
+        panel count (0: CSR tiles), panel width, pseudo-rows and warp tiles."""
+        arrs = [(ctypes.c_int64 * 2)() for _ in range(4)]
+        _check(self._L.pdhg_get_layout(self._ctx, *arrs))
+        keys = ["panels", "panel_width", "pseudo_rows", "tiles"]
+        return {side: {k: int(a[j]) for k, a in zip(keys, arrs)} for j, side in enumerate(["a", "at"])}
 
     def gather_floor(self, on_a: bool, reps: int = 10) -> float:
         """Mean ms of the row-logic-free gather pass over A~ (on_a) or A~^T."""

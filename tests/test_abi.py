@@ -73,3 +73,35 @@ def test_header_is_plain_c(tmp_path):
                         "-I", os.path.join(ROOT, "include"), "-o", str(tmp_path / "abi_check.o")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_options_struct_matches_the_header(tmp_path):
+    """The ctypes mirror of pdhg_options has the C struct's size and every
+    field at the C offset (a field added to one and not the other fails)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2603_03150_gb300 import pdhg
+    names = [f[0] for f in pdhg.Options._fields_]
+    lines = "\n".join(f'  printf("{n} %zu\\n", offsetof(pdhg_options, {n}));' for n in names)
+    src = tmp_path / "opt_layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pdhg.h"\n'
+                   "int main(void) {\n" + lines +
+                   '\n  printf("sizeof %zu\\n", sizeof(pdhg_options));\n  return 0;\n}\n')
+    exe = tmp_path / "opt_layout"
+    r = subprocess.run(["gcc", "-std=c99", str(src), "-I", os.path.join(ROOT, "include"),
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    for n in names:
+        assert int(got[n]) == getattr(pdhg.Options, n).offset, n
+    assert int(got["sizeof"]) == ctypes.sizeof(pdhg.Options)
+
+
+def test_default_layout_options(libpath):
+    from paper_2603_03150_gb300 import pdhg
+    o = pdhg.Options()
+    pdhg.lib().pdhg_default_options(ctypes.byref(o))
+    assert o.spmv_layout == 0 and o.panel_width == 0 and o.method == 0
