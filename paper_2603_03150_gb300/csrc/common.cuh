@@ -228,6 +228,19 @@ __device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
   return r;
 }
 
+// Asynchronous L2 prefetch of [p, p + bytes) by the bulk-copy engine (one
+// thread issues it; no registers wait on it).  The range is widened to 16-byte
+// boundaries, so the array must have 16 bytes to spare past its end.
+__device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes) {
+  if (bytes <= 0) return;
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(15);
+  const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + (uintptr_t)bytes + 15) & ~uintptr_t(15);
+  for (uintptr_t a = lo; a < hi; a += 65536) {
+    const uint32_t sz = (uint32_t)((hi - a) < 65536 ? (hi - a) : 65536);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(sz) : "memory");
+  }
+}
+
 // Programmatic dependent launch: a half-step kernel launched with the
 // programmatic-serialization attribute may become resident while the kernel
 // before it drains; it lets its own successor do the same, then waits for

@@ -148,7 +148,7 @@ pdhg_status pdhg::upload_sched(pdhg_ctx* ctx, const HostSched& h, DevSched* d,
   CKS(dalloc(ctx, &d->counters, h.groups.size()));
   CKS(dalloc(ctx, &d->slots, (size_t)h.total_parts * 2));
   // 32-bit words up to 16 nonzeros per thread, 64-bit words beyond
-  CKS(dalloc(ctx, &d->wd, (size_t)h.nwords * (h.e > 16 ? 2 : 1)));
+  CKS(dalloc(ctx, &d->wd, (size_t)h.nwords * (h.e > 16 ? 2 : 1) + 4));  // spare: L2 prefetches
   if (!h.tiles.empty())
     CK(cudaMemcpyAsync(d->tiles, h.tiles.data(), h.tiles.size() * sizeof(Tile),
                        cudaMemcpyHostToDevice, ctx->stream));

@@ -221,6 +221,11 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
 
   for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
     const Tile tl = S.tiles[t];
+    // the block's next tile: its descriptor now, its nonzeros and window
+    // words prefetched into L2 once this tile's own loads are out
+    const bool has_next = tid == 0 && t + (int)gridDim.x < S.ntiles;
+    Tile nx{};
+    if (has_next) nx = S.tiles[t + gridDim.x];
     if (!epi_begin(epi, tl, 0)) continue;
     const int nzb = tl.nz_begin, nze = tl.nz_end;
     const int nrows = tl.row_end - tl.row_begin;
@@ -302,6 +307,12 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
       }
     }
 
+    if (has_next) {
+      prefetch_l2(col + nx.nz_begin, 4LL * (nx.nz_end - nx.nz_begin));
+      prefetch_l2(val + nx.nz_begin, (int64_t)sizeof(T) * (nx.nz_end - nx.nz_begin));
+      if (nx.split < 0 && nx.nz_end > nx.nz_begin)
+        prefetch_l2(wd + nx.word0, (int64_t)sizeof(W) * BLOCK);
+    }
     if (tl.split >= 0) {
       split_chunk<T, NV, BLOCK>(S, tl, acc, epi, wsum);
       epi_end(epi, tl, t, 0);
