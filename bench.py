@@ -235,7 +235,7 @@ def run_ours(args):
         src = devt if device_io else pinned
         s = pdhg.Solver(m, n, src["row_ptr"], src["col"], src["val"], src["b"], src["c"],
                         precision=precision, device_io=device_io, stream=stream.cuda_stream,
-                        kernel_timing=timing, method=args.method)
+                        kernel_timing=timing, method=args.method, spmv_layout=args.layout)
         st = s.solve(EPS, args.max_iter)
         g = s.get(out=outs[0] if outs else None)
         w = s.warmstart_point(unscaled=True, out=outs[1] if outs else None)
@@ -371,7 +371,7 @@ def run_ours(args):
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "precision": args.precision +
                        ("_mixed (f64 norms, gap, restart rule, step/weight updates)" if args.precision == "fp32" else ""),
-                       "eps_rel": EPS, "method": args.method,
+                       "eps_rel": EPS, "method": args.method, "layout": args.layout,
                        "step": "create + solve to eps + get + warmstart_point",
                        "l2": "flushed between steps (512 MiB write), inputs resident in HBM",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
@@ -757,6 +757,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="powerlaw")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--layout", choices=["auto", "csr", "panels"], default="auto",
+                    help="FP32 half-step layout: autotuned (default), CSR tiles or column panels")
     ap.add_argument("--method", choices=["averaged", "halpern"], default="averaged",
                     help="PDHG iteration: restarted averaged (default) or reflected Halpern")
     ap.add_argument("--fp64-steps", type=int, default=1)
