@@ -91,9 +91,10 @@ typedef struct pdhg_options {
   double reflection;       /* rho of method 1, in [0, 1] (default 1)           */
   int32_t spmv_layout;     /* FP32_MIXED single-LP half-steps (the products
                               A~^T y and A~ x+ of Section 2's iteration):
-                              0 (default): per matrix, the faster of the CSR
-                              tiles and the column panels, timed at create
-                              when autotune is on (CSR tiles otherwise);
+                              0 (default): the faster combination of CSR
+                              tiles and column panels, timed at create when
+                              autotune is on and nnz >= 2^20 (CSR tiles
+                              otherwise);
                               1: CSR tiles only; 2: column panels wherever
                               they apply.  Column panels stage a slice of the
                               gathered vector in shared memory and apply when

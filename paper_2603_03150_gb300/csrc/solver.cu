@@ -456,10 +456,13 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
                                 smem_for(0, mx, best.view.max_rows, best.view.e), best.view.ntiles);
 
     // column panels where they apply: forced (spmv_layout 2), or candidates
-    // timed below against the CSR tiles picked above (autotune on, tile_nnz 0)
+    // timed below against the CSR tiles picked above (autotune on, tile_nnz 0,
+    // and at least 2^20 nonzeros: below that the gathered vectors live in L1/L2
+    // anyway and building the panels costs more create time than it saves)
     const int lay = ctx->opt.spmv_layout;
     int pw = 0, np = 0;
-    if ((lay == 2 || (lay == 0 && cands.size() > 1)) && panel_shape(ctx, on_a, &pw, &np)) {
+    const bool auto_panels = lay == 0 && cands.size() > 1 && ctx->nnz >= (int64_t(1) << 20);
+    if ((lay == 2 || auto_panels) && panel_shape(ctx, on_a, &pw, &np)) {
       DevPanel& dp = on_a ? ctx->pa : ctx->pt;
       CKS(build_panel_layout(ctx, on_a, &dp));
       const int rows = on_a ? ctx->m : ctx->n;
