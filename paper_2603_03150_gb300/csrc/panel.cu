@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   float* part = V.partial + (size_t)bd.panel * V.rows;
   while (t < bd.t_end) {
     const PanelTile tl = cur.tl;
+    int t_next = -1;  // set once the next tile's loads are issued
     if (tl.nps < 0) {  // one long pseudo-row: lanes stride over it, then a warp sum
       float acc = 0.f;
       for (int base = tl.nz_begin + lane * 8; base < tl.nz_begin + tl.nz_len; base += 8 * 32) {
@@ -205,6 +206,15 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       }
       const int key = (active && !((d >> 7) & 1u)) ? r : -1;  // pseudo-row open at the window's end
       if (!active) head_row = -1;
+      // the tile's values, columns and gathers are dead: the next tile's loads
+      // go out now and overlap the scan, the head fix-up and the staged writes
+      {
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(next_tile, 1);
+        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+        t_next = nxt;
+        if (nxt < bd.t_end) panel_load(cur, V, dc, bd.t_begin, nxt, lane, pol);
+      }
       // segmented inclusive scan of the open sums (equal keys are adjacent lanes)
       float sv = acc;
 #pragma unroll
@@ -230,10 +240,13 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       }
       __syncwarp();
     }
-    int nxt = 0;
-    if (lane == 0) nxt = atomicAdd(next_tile, 1);
-    t = __shfl_sync(0xffffffffu, nxt, 0);
-    if (t < bd.t_end) panel_load(cur, V, dc, bd.t_begin, t, lane, pol);
+    if (t_next < 0) {  // a long tile: the next tile's loads go out here
+      int nxt = 0;
+      if (lane == 0) nxt = atomicAdd(next_tile, 1);
+      t_next = __shfl_sync(0xffffffffu, nxt, 0);
+      if (t_next < bd.t_end) panel_load(cur, V, dc, bd.t_begin, t_next, lane, pol);
+    }
+    t = t_next;
   }
 }
 
