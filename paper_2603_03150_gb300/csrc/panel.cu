@@ -72,9 +72,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const PanelBlock bd = V.blocks[blockIdx.x];
   const uint64_t pol = stream_policy();
-  // the layout is constant: the first tile's loads are issued before waiting
-  // for the kernel that produced v
-  // the block's tiles are contiguous: one thread hands their nonzeros, window
+  // the layout is constant, so everything up to pdl_enter() may overlap the
+  // kernel that produces v.  The block's tiles are contiguous: one thread
+  // hands their nonzeros, window
   // words and rows to the bulk-copy engine as L2 prefetches (16 KB pieces,
   // the four arrays interleaved in the order the warps consume them)
   if (tid == 0) {
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   if (tid == 0) *next_tile = bd.t_begin + kPanelWarps;
   __syncthreads();
   int t = bd.t_begin + warp;
-  PanelLoad cur;
+  PanelLoad cur;  // the first tile's loads go out before the wait
   if (t < bd.t_end) panel_load(cur, V, dc, bd.t_begin, t, lane, pol);
   pdl_enter();
   if (sc->done) return;

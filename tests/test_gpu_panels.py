@@ -229,3 +229,29 @@ def test_full_size_powerlaw_matches_oracle():
         _state_close(st, r.state, 1e-4)
         assert [(e["k"], e["restart"], e["cand"]) for e in lg] == \
                [(e["k"], e["restart"], e["cand"]) for e in r.log]
+
+
+def test_panels_are_deterministic_and_resume_from_a_checkpoint():
+    """The panel sums have a fixed order: two contexts give bit-identical
+    iterates, and a run checkpointed at k = 128 (an evaluation point, so the
+    evaluations of both runs coincide) and resumed in a new context ends
+    where the uninterrupted run does."""
+    lp = heavy_row_lp(3)
+    kw = dict(precision="fp32", spmv_layout="panels", panel_width=2048)
+    runs = []
+    for _ in range(2):
+        with pdhg.Solver.from_lp(lp, **kw) as s:
+            s.solve(1e-12, 320)
+            runs.append(s.state())
+    for k in ("x", "y", "x_avg", "y_avg"):
+        assert np.array_equal(runs[0][k], runs[1][k]), k
+    with pdhg.Solver.from_lp(lp, **kw) as s1:
+        s1.solve(1e-12, 128)
+        ck = s1.state()
+    with pdhg.Solver.from_lp(lp, **kw) as s2:
+        s2.set_state(ck)
+        s2.solve(1e-12, 320)
+        got = s2.state()
+    for k in ("x", "y", "x_avg", "y_avg"):
+        assert np.array_equal(got[k], runs[0][k]), k
+    assert got["k"] == runs[0]["k"] == 320 and got["restarts"] == runs[0]["restarts"]
