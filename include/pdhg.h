@@ -170,7 +170,10 @@ pdhg_status pdhg_get_transpose(pdhg_ctx* ctx, int32_t* row_ptr_t, int32_t* col_t
 
 /* Checkpoint: scaled iterate x[n], y[m], running averages, last restart point,
  * and scalars[8] = {omega, k, t, restarts, kkt_last, kkt_prev, eta, 0}.
- * pdhg_set_state restores the same fields (Ax caches are recomputed).  */
+ * pdhg_set_state restores the same fields; the A~x caches (of x, of the
+ * running average and of the restart point) are recomputed by one SpMV each,
+ * so a resumed run matches an uninterrupted one up to the rounding of those
+ * caches (the cached average of A~x is not A~ x_avg bit for bit).  */
 pdhg_status pdhg_get_state(pdhg_ctx* ctx, double* x, double* y, double* x_avg,
                            double* y_avg, double* x_last, double* y_last, double* scalars);
 pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const double* y,
