@@ -170,15 +170,24 @@ pdhg_status pdhg_get_transpose(pdhg_ctx* ctx, int32_t* row_ptr_t, int32_t* col_t
 
 /* Checkpoint: scaled iterate x[n], y[m], running averages, last restart point,
  * and scalars[8] = {omega, k, t, restarts, kkt_last, kkt_prev, eta, 0}.
- * pdhg_set_state restores the same fields; the A~x caches (of x, of the
- * running average and of the restart point) are recomputed by one SpMV each,
- * so a resumed run matches an uninterrupted one up to the rounding of those
- * caches (the cached average of A~x is not A~ x_avg bit for bit).  */
+ * pdhg_set_state restores the same fields and recomputes the A~x caches (of
+ * x, of the running average and of the restart point) by one SpMV each, so a
+ * resumed run matches an uninterrupted one up to the rounding of those caches
+ * (the cached average of A~x is not A~ x_avg bit for bit) unless the caches
+ * are restored too (pdhg_get_caches / pdhg_set_caches).  */
 pdhg_status pdhg_get_state(pdhg_ctx* ctx, double* x, double* y, double* x_avg,
                            double* y_avg, double* x_last, double* y_last, double* scalars);
 pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const double* y,
                            const double* x_avg, const double* y_avg, const double* x_last,
                            const double* y_last, const double* scalars);
+
+/* The A~x caches of a checkpoint, float64 [m] each (HOST or device as the
+ * other arrays; NULL skips): A~x of the iterate, the running average of A~x
+ * and A~x of the last restart point.  pdhg_set_caches after pdhg_set_state
+ * makes a resumed run repeat the uninterrupted one bit for bit.  */
+pdhg_status pdhg_get_caches(pdhg_ctx* ctx, double* Ax, double* Ax_avg, double* Ax_last);
+pdhg_status pdhg_set_caches(pdhg_ctx* ctx, const double* Ax, const double* Ax_avg,
+                            const double* Ax_last);
 
 /* Evaluation log of the restart rule (one entry per evaluation with k % F == 0
  * that did not terminate; up to `cap` entries, oldest first):

@@ -1331,6 +1331,37 @@ extern "C" pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const doub
   return PDHG_OK;
 }
 
+extern "C" pdhg_status pdhg_get_caches(pdhg_ctx* ctx, double* Ax, double* Ax_avg,
+                                       double* Ax_last) {
+  g_last_error.clear();
+  if (!ctx || ctx->batch) {
+    set_error("pdhg_get_caches needs a single-LP context");
+    return PDHG_INVALID_ARG;
+  }
+  const int m = ctx->m;
+  CKS(state_out(ctx, Ax, ctx->Ax, m));
+  CKS(state_out(ctx, Ax_avg, ctx->Ax_avg, m));
+  CKS(state_out(ctx, Ax_last, ctx->Ax_last, m));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_set_caches(pdhg_ctx* ctx, const double* Ax, const double* Ax_avg,
+                                       const double* Ax_last) {
+  g_last_error.clear();
+  if (!ctx || ctx->batch) {
+    set_error("pdhg_set_caches needs a single-LP context");
+    return PDHG_INVALID_ARG;
+  }
+  const int m = ctx->m;
+  CKS(state_in(ctx, ctx->Ax, Ax, m));
+  CKS(state_in(ctx, ctx->Ax_avg, Ax_avg, m));
+  CKS(state_in(ctx, ctx->Ax_last, Ax_last, m));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->report_valid = false;
+  return PDHG_OK;
+}
+
 extern "C" pdhg_status pdhg_get_log(pdhg_ctx* ctx, int32_t cap, int32_t* count, int64_t* k,
                                     int32_t* flags, double* kkt) {
   g_last_error.clear();

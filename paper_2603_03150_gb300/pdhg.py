@@ -87,6 +87,8 @@ _SIGS = {
     "pdhg_get_kernel_timing": (_I32, [_P, _P, _P, _P]),
     "pdhg_get_schedule": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pdhg_get_layout": (_I32, [_P, _P, _P, _P, _P]),
+    "pdhg_get_caches": (_I32, [_P, _P, _P, _P]),
+    "pdhg_set_caches": (_I32, [_P, _P, _P, _P]),
     "pdhg_get_kernel_timing_parts": (_I32, [_P, _P, _P]),
     "pdhg_get_launch_count": (_I32, [_P, _P]),
     "pdhg_gather_floor": (_I32, [_P, _I32, _I32, _P]),
@@ -285,6 +287,9 @@ class Solver:
         _check(self._L.pdhg_get_state(self._ctx, *[_ptr(a) for a in arrs], _ptr(sc)))
         keys = ["x", "y", "x_avg", "y_avg", "x_last", "y_last"]
         d = dict(zip(keys, arrs))
+        caches = [self._new(m), self._new(m), self._new(m)]
+        _check(self._L.pdhg_get_caches(self._ctx, *[_ptr(a) for a in caches]))
+        d.update(zip(["Ax", "Ax_avg", "Ax_last"], caches))
         d.update(omega=sc[0], k=int(sc[1]), t=int(sc[2]), restarts=int(sc[3]),
                  kkt_last=sc[4], kkt_prev=sc[5], eta=sc[6])
         return d
@@ -297,6 +302,11 @@ class Solver:
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
         _check(self._L.pdhg_set_state(self._ctx, *[_ptr(a) for a in arrs], _ptr(sc)),
                allow_positive=False)
+        if all(k in st for k in ("Ax", "Ax_avg", "Ax_last")):
+            caches = [st[k] for k in ("Ax", "Ax_avg", "Ax_last")]
+            if not self.device_io:
+                caches = [np.ascontiguousarray(a, dtype=np.float64) for a in caches]
+            _check(self._L.pdhg_set_caches(self._ctx, *[_ptr(a) for a in caches]))
 
     def log(self, cap: int = 4096):
         cnt = _I32()
