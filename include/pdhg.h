@@ -184,7 +184,10 @@ pdhg_status pdhg_set_state(pdhg_ctx* ctx, const double* x, const double* y,
 /* The A~x caches of a checkpoint, float64 [m] each (HOST or device as the
  * other arrays; NULL skips): A~x of the iterate, the running average of A~x
  * and A~x of the last restart point.  pdhg_set_caches after pdhg_set_state
- * makes a resumed run repeat the uninterrupted one bit for bit.  */
+ * makes a resumed run repeat the uninterrupted one bit for bit, for a
+ * checkpoint taken at an iteration count that is not a multiple of
+ * eval_freq (a solve that stops at max_iter = j * eval_freq does not apply
+ * that evaluation's restart decision; the uninterrupted run does).  */
 pdhg_status pdhg_get_caches(pdhg_ctx* ctx, double* Ax, double* Ax_avg, double* Ax_last);
 pdhg_status pdhg_set_caches(pdhg_ctx* ctx, const double* Ax, const double* Ax_avg,
                             const double* Ax_last);
