@@ -568,7 +568,7 @@ def run_sweep(args):
     out = {}
     launches = 0
     with Clocks(local) as clk:
-        for prec in ("fp64", "fp32"):
+        for prec in args.sweep_precisions.split(","):
             rows = []
             for eps in (1e-4, 1e-6, 1e-8):
                 ms, its, sts, viol = [], [], [], []
@@ -581,7 +581,8 @@ def run_sweep(args):
                     e0.record(stream)
                     s = pdhg.Solver(lp.m, lp.n, devt["row_ptr"], devt["col"], devt["val"],
                                     devt["b"], devt["c"], precision=prec, device_io=True,
-                                    stream=stream.cuda_stream, method=args.method)
+                                    stream=stream.cuda_stream, method=args.method,
+                                    spmv_layout=args.layout)
                     st = s.solve(eps, args.max_iter)
                     s.get()
                     e1.record(stream)
@@ -601,12 +602,13 @@ def run_sweep(args):
             for r in rows:
                 r["time_vs_1e-4"] = round(r["time_s"] / t0, 3) if t0 > 0 else None
             out[prec] = rows
-    value = out["fp64"][-1]["time_s"]
+    head = "fp64" if "fp64" in out else next(iter(out))
+    value = out[head][-1]["time_s"]
     line = {"metric": "tolerance sweep: time to eps_rel and max violation (FP64, FP32-mixed)",
-            "value": value, "unit": "s (FP64, eps_rel = 1e-8)", "n_gpus": 1, "steps": args.steps,
-            "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "method": args.method,
+            "value": value, "unit": f"s ({head.upper()}, eps_rel = 1e-8)", "n_gpus": 1,
+            "steps": args.steps, "warmup": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "method": args.method, "layout": args.layout,
                        "step": "create + solve to eps + get", "max_iter": args.max_iter,
                        "l2": "flushed between solves (512 MiB write)"},
             "sweep": out, "gpu_launches": launches, "clocks": clk.summary()}
@@ -757,6 +759,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="powerlaw")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--sweep-precisions", default="fp64,fp32",
+                    help="precisions of --eps-sweep, comma-separated")
     ap.add_argument("--layout", choices=["auto", "csr", "panels"], default="auto",
                     help="FP32 half-step layout: autotuned (default), CSR tiles or column panels")
     ap.add_argument("--method", choices=["averaged", "halpern"], default="averaged",
