@@ -326,8 +326,9 @@ pdhg_status pdhg_get_launch_count(pdhg_ctx* ctx, int64_t* launches);
  * primal (on_a = 0: A~^T, gathering y) kernel that keeps only the memory work -
  * 128-bit loads of column indices and values with the same cache policy, the
  * random gathers and one multiply-add each - and no row logic, scan or
- * epilogue: the gather-rate floor the SpMV kernels are measured against.
- * Single-LP contexts; leaves the solver state unchanged.  */
+ * epilogue: the floor of gathering through L1/L2, which bounds the CSR-tile
+ * kernels (the column-panel half-steps gather from shared memory and can go
+ * below it).  Single-LP contexts; leaves the solver state unchanged.  */
 pdhg_status pdhg_gather_floor(pdhg_ctx* ctx, int32_t on_a, int32_t reps, double* ms);
 
 void pdhg_destroy(pdhg_ctx* ctx);
