@@ -49,7 +49,8 @@ struct SchedView {
 // Column-panel layout of one matrix (float32 iterations).  The columns are cut
 // into panels of P; the nonzeros of row i inside panel p form pseudo-row
 // (p, i).  Pseudo-rows are ordered by (panel, row) and packed whole into warp
-// tiles of at most kPanelCap nonzeros, padded with zeros to a multiple of 8;
+// tiles of at most kPanelCap nonzeros and `pscap` (128 or 256) pseudo-rows,
+// padded with zeros to a multiple of 8;
 // a pseudo-row longer than kPanelCap is a tile of its own (nps < 0).  Each
 // block stages one panel of the gathered vector in shared memory and runs a
 // contiguous range of that panel's tiles; each pseudo-row's sum goes to
@@ -57,7 +58,7 @@ struct SchedView {
 // ---------------------------------------------------------------------------
 constexpr int kPanelWarps = 32;                 // warps of a panel block
 constexpr int kPanelCap = 256;                  // nonzeros of a warp tile
-constexpr int kPanelStage = kPanelWarps * kPanelCap;  // staged sums per block (floats)
+constexpr int kPanelPsCap = 256;                // pseudo-rows of a warp tile, at most
 constexpr int kPanelDescCache = 256;            // tile descriptors a block keeps in shared memory
 
 struct PanelTile {
@@ -80,6 +81,8 @@ struct PanelView {
   const int32_t* psrow; // row of each pseudo-row
   float* partial;       // [npanels][rows]
   int32_t P, npanels, rows, cols, nblocks, ntiles;
+  int32_t pscap;        // pseudo-rows of a tile at most (128 or 256): the staged sums per warp
+  int32_t pad;
 };
 
 // ---------------------------------------------------------------------------

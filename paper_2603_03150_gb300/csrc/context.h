@@ -204,9 +204,10 @@ pdhg_status upload_lp(pdhg_ctx* ctx, const int32_t* col, const double* val, cons
 pdhg_status prepare_matrix(pdhg_ctx* ctx);
 pdhg_status polling_resources(pdhg_ctx* ctx);
 // column panels (panel.cu): the panel width and count for the rows of A~
-// (on_a) or A~^T, false where the panels do not apply (float64, batches, or
-// dense partial sums above about twice the nonzeros); the device layout
-bool panel_shape(const pdhg_ctx* ctx, bool on_a, int* P, int* npanels);
+// (on_a) or A~^T with tiles of at most `pscap` pseudo-rows, false where the
+// panels do not apply (float64, batches, or dense partial sums above about
+// twice the nonzeros); the device layout
+bool panel_shape(const pdhg_ctx* ctx, bool on_a, int* P, int* npanels, int pscap = 256);
 pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out);
 
 }  // namespace pdhg

@@ -159,7 +159,7 @@ cudaError_t configure_tile_kernels(size_t max_smem);
 // `between` (optional) is recorded between the two kernels
 void launch_panel_half(const IterBuffers<float>& B, const PanelView& V, bool dual, int method,
                        int row_grid, int i, cudaStream_t s, cudaEvent_t between = nullptr);
-size_t panel_smem(int P);
+size_t panel_smem(int P, int pscap);
 // blocks of 256 threads for the row pass over `rows` rows of `npanels` panels
 int panel_row_grid(int rows, int npanels, int nsm);
 cudaError_t configure_panel_kernels(size_t max_smem);

@@ -65,10 +65,11 @@ __device__ __forceinline__ int col16(const int4& cc, int e) {
 __global__ void __launch_bounds__(kPanelThreads, 1)
     k_panel_spmv(PanelView V, const float* __restrict__ v, const Scalars* __restrict__ sc) {
   extern __shared__ __align__(16) float smem[];
-  float* stage = smem;               // [warps][kPanelCap] pseudo-row sums
-  PanelTile* dc = reinterpret_cast<PanelTile*>(smem + kPanelStage);  // the first tiles of the block
-  int* next_tile = reinterpret_cast<int*>(smem + kPanelStage + 4 * kPanelDescCache);
-  float* vs = smem + kPanelStage + 4 * kPanelDescCache + 4;           // the panel of v
+  const int stage_len = kPanelWarps * V.pscap;
+  float* stage = smem;               // [warps][pscap] pseudo-row sums
+  PanelTile* dc = reinterpret_cast<PanelTile*>(smem + stage_len);  // the first tiles of the block
+  int* next_tile = reinterpret_cast<int*>(smem + stage_len + 4 * kPanelDescCache);
+  float* vs = smem + stage_len + 4 * kPanelDescCache + 4;           // the panel of v
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const PanelBlock bd = V.blocks[blockIdx.x];
   const uint64_t pol = stream_policy();
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     for (int q = (n4 << 2) + tid; q < cnt; q += kPanelThreads) vs[q] = __ldg(v + c0 + q);
   }
   __syncthreads();
-  float* st = stage + warp * kPanelCap;
+  float* st = stage + warp * V.pscap;
   float* part = V.partial + (size_t)bd.panel * V.rows;
   while (t < bd.t_end) {
     const PanelTile tl = cur.tl;
@@ -163,9 +164,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       // rows of this tile's pseudo-rows (at most 8 per lane), loaded before
       // the gathers; slots past the tile's pseudo-rows are skipped warp-wide
       const int nps = tl.nps;
-      int rid[kPanelCap / 32];
+      int rid[kPanelPsCap / 32];
 #pragma unroll
-      for (int j = 0; j < kPanelCap / 32; ++j) {
+      for (int j = 0; j < kPanelPsCap / 32; ++j) {
         rid[j] = 0;
         if (32 * j < nps) {
           const int k = lane + 32 * j;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       }
       __syncwarp();
 #pragma unroll
-      for (int j = 0; j < kPanelCap / 32; ++j) {
+      for (int j = 0; j < kPanelPsCap / 32; ++j) {
         if (32 * j < nps) {
           const int k = lane + 32 * j;
           if (k < nps) part[rid[j]] = st[k];
@@ -391,14 +392,15 @@ int panel_lanes(int np) {
     } break;                         \
   }
 
-size_t panel_smem(int P) {
-  return sizeof(float) * ((size_t)kPanelStage + 4 * (size_t)kPanelDescCache + 4 + (size_t)P);
+size_t panel_smem(int P, int pscap) {
+  return sizeof(float) *
+         ((size_t)kPanelWarps * pscap + 4 * (size_t)kPanelDescCache + 4 + (size_t)P);
 }
 
 void launch_panel_half(const IterBuffers<float>& B, const PanelView& V, bool dual, int method,
                        int row_grid, int i, cudaStream_t s, cudaEvent_t between) {
   const float* v = dual ? (method == 1 ? B.x_avg : B.x) : B.y;
-  launch_pdl(k_panel_spmv, V.nblocks, kPanelThreads, panel_smem(V.P), s, V, v,
+  launch_pdl(k_panel_spmv, V.nblocks, kPanelThreads, panel_smem(V.P, V.pscap), s, V, v,
              (const Scalars*)B.sc);
   if (between) cudaEventRecordWithFlags(between, s, cudaEventRecordExternal);
   const int g = panel_lanes(V.npanels);
@@ -476,7 +478,8 @@ __global__ void k_pl_panel_first(int np, int R, const int32_t* __restrict__ psid
 template <bool kEmit>
 __global__ void k_pl_pack(int nseg, const int2* __restrict__ segs, const int32_t* __restrict__ seg_panel,
                           const int32_t* __restrict__ pslen, const int32_t* __restrict__ toff,
-                          int32_t* tcount, PanelTile* tiles, int32_t* tlen, int32_t* tpanel) {
+                          int pscap, int32_t* tcount, PanelTile* tiles, int32_t* tlen,
+                          int32_t* tpanel) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
   const int b = segs[s].x, e = segs[s].y;
@@ -490,7 +493,9 @@ __global__ void k_pl_pack(int nseg, const int2* __restrict__ segs, const int32_t
       ++k;
     } else {
       int used = 0;
-      while (k < e && pslen[k] <= kPanelCap && used + pslen[k] <= kPanelCap) used += pslen[k++];
+      while (k < e && pslen[k] <= kPanelCap && used + pslen[k] <= kPanelCap &&
+             k - tl.ps_begin < pscap)
+        used += pslen[k++];
       tl.nz_len = (used + 7) & ~7;
       tl.nps = k - tl.ps_begin;
     }
@@ -608,13 +613,13 @@ struct Tmp {  // device scratch freed with the object
 
 }  // namespace
 
-bool panel_shape(const pdhg_ctx* ctx, bool on_a, int* P_out, int* np_out) {
+bool panel_shape(const pdhg_ctx* ctx, bool on_a, int* P_out, int* np_out, int pscap) {
   if (!ctx->mixed || ctx->batch || ctx->nnz < 1) return false;
   const int64_t R = on_a ? ctx->m : ctx->n, C = on_a ? ctx->n : ctx->m;
   if (R < 1 || C < 1 || ctx->nnz > (int64_t(1) << 30)) return false;
-  int64_t pmax =
-      ((int64_t)ctx->smem_optin / (int64_t)sizeof(float) - kPanelStage - 4 * kPanelDescCache - 4) &
-      ~int64_t(7);
+  int64_t pmax = ((int64_t)ctx->smem_optin / (int64_t)sizeof(float) - (int64_t)kPanelWarps * pscap -
+                  4 * kPanelDescCache - 4) &
+                 ~int64_t(7);
   pmax = std::min<int64_t>(pmax, 65536);
   if (pmax < 1024) return false;
   if (ctx->opt.panel_width > 0) pmax = std::min<int64_t>(pmax, std::max(8, ctx->opt.panel_width & ~7));
@@ -639,7 +644,7 @@ bool panel_shape(const pdhg_ctx* ctx, bool on_a, int* P_out, int* np_out) {
 pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   *out = DevPanel{};
   int P = 0, np = 0;
-  if (!panel_shape(ctx, on_a, &P, &np)) {
+  if (!panel_shape(ctx, on_a, &P, &np, 256)) {
     set_error("column panels do not apply to this matrix");
     return PDHG_INVALID_ARG;
   }
@@ -648,28 +653,45 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   const int32_t* rp = on_a ? ctx->a_rp : ctx->t_rp;
   const int32_t* col = on_a ? ctx->a_col : ctx->t_col;
   const float* val = on_a ? ctx->a_val32 : ctx->t_val32;
-  const int64_t len = (int64_t)np * R;
+  int64_t len = (int64_t)np * R;  // the 256 cap gives the narrowest panels: the most of them
 
-  // pseudo-rows: counts per (panel, row), their prefix, the compacted list
-  Tmp<int32_t> cnt, src, flag, psidx, scan_tmp;
+  // pseudo-rows: counts per (panel, row), their prefix, the first of each panel
+  Tmp<int32_t> cnt, src, flag, psidx, scan_tmp, pfirst;
   PL_CK(cnt.alloc(len));
   PL_CK(src.alloc(len));
   PL_CK(flag.alloc(len));
   PL_CK(psidx.alloc(len + 1));
   PL_CK(scan_tmp.alloc(len / 1024 + 2 + 1024));
-  PL_CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * len, s));
-  k_pl_count<<<grid_for((int64_t)R * 32), 256, 0, s>>>(R, rp, col, P, cnt.p, src.p);
-  k_pl_flag<<<grid_for(len), 256, 0, s>>>(len, cnt.p, flag.p);
-  launch_scan(flag.p, psidx.p, (int)len, scan_tmp.p, s);
-  Tmp<int32_t> pfirst;
   PL_CK(pfirst.alloc(np + 1));
-  k_pl_panel_first<<<(np + 256) / 256, 256, 0, s>>>(np, R, psidx.p, pfirst.p);
-  std::vector<int32_t> h_pfirst(np + 1);
-  PL_CK(cudaMemcpyAsync(h_pfirst.data(), pfirst.p, sizeof(int32_t) * (np + 1),
-                        cudaMemcpyDeviceToHost, s));
-  PL_CK(cudaStreamSynchronize(s));
+  std::vector<int32_t> h_pfirst;
+  auto count = [&](int P_, int np_) -> pdhg_status {
+    const int64_t len_ = (int64_t)np_ * R;
+    PL_CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * len_, s));
+    k_pl_count<<<grid_for((int64_t)R * 32), 256, 0, s>>>(R, rp, col, P_, cnt.p, src.p);
+    k_pl_flag<<<grid_for(len_), 256, 0, s>>>(len_, cnt.p, flag.p);
+    launch_scan(flag.p, psidx.p, (int)len_, scan_tmp.p, s);
+    k_pl_panel_first<<<(np_ + 256) / 256, 256, 0, s>>>(np_, R, psidx.p, pfirst.p);
+    h_pfirst.assign(np_ + 1, 0);
+    PL_CK(cudaMemcpyAsync(h_pfirst.data(), pfirst.p, sizeof(int32_t) * (np_ + 1),
+                          cudaMemcpyDeviceToHost, s));
+    PL_CK(cudaStreamSynchronize(s));
+    ctx->launches += 6;
+    return PDHG_OK;
+  };
+  CKS(count(P, np));
+  // A tile holds at most 256 nonzeros: when it holds fewer than 96 pseudo-rows
+  // on average, a cap of 128 pseudo-rows rarely binds, and the halved staging
+  // of the sums buys wider panels (fewer panels, pseudo-rows and partial sums).
+  int pscap = 256, P128 = 0, np128 = 0;
+  if ((double)kPanelCap * (double)h_pfirst[np] < 96.0 * (double)ctx->nnz &&
+      panel_shape(ctx, on_a, &P128, &np128, 128) && P128 != P) {
+    pscap = 128;
+    P = P128;
+    np = np128;
+    len = (int64_t)np * R;
+    CKS(count(P, np));
+  }
   const int nps = h_pfirst[np];
-  ctx->launches += 6;
   CKS(dalloc(ctx, &out->psrow, (size_t)nps + 16));  // spare: prefetches round up to 16 bytes
   Tmp<int32_t> pslen, pssrc;
   PL_CK(pslen.alloc(nps));
@@ -698,7 +720,7 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
     PL_CK(cudaMemcpyAsync(seg_panel.p, h_seg_panel.data(), sizeof(int32_t) * nseg,
                           cudaMemcpyHostToDevice, s));
     k_pl_pack<false><<<(nseg + 127) / 128, 128, 0, s>>>(nseg, segs.p, seg_panel.p, pslen.p,
-                                                         nullptr, tcount.p, nullptr, nullptr,
+                                                         nullptr, pscap, tcount.p, nullptr, nullptr,
                                                          nullptr);
   }
   launch_scan(tcount.p, toff.p, nseg, scan_tmp.p, s);
@@ -714,7 +736,7 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   PL_CK(nzoff.alloc(nt + 1));
   if (nseg > 0)
     k_pl_pack<true><<<(nseg + 127) / 128, 128, 0, s>>>(nseg, segs.p, seg_panel.p, pslen.p, toff.p,
-                                                        nullptr, out->tiles, tlen.p, tpanel.p);
+                                                        pscap, nullptr, out->tiles, tlen.p, tpanel.p);
   launch_scan(tlen.p, nzoff.p, nt, scan_tmp.p, s);
   if (nt > 0) k_pl_tile_begin<<<(nt + 255) / 256, 256, 0, s>>>(nt, nzoff.p, out->tiles);
   std::vector<int32_t> h_nzoff(nt + 1);
@@ -811,6 +833,7 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   V.cols = C;
   V.nblocks = nb;
   V.ntiles = nt;
+  V.pscap = pscap;
   out->pseudo_rows = nps;
   out->nnz_padded = nzp;
   out->on = nb > 0;
