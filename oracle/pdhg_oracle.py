@@ -242,6 +242,51 @@ def max_violation(A, b, c, x, y) -> float:
 
 
 # ---------------------------------------------------------------------------
+# a8: the restart rule and the primal-weight update, as pure functions of the
+# scalars of one evaluation (the loop below calls them; tests pin them by hand)
+# ---------------------------------------------------------------------------
+def restart_decision(kkt_cur: float, kkt_avg: float, kkt_last: float, kkt_prev: float,
+                     t: int, k: int, opts: Optional["Options"] = None) -> dict:
+    """One evaluation of the KKT restart rule (the cuPDLP reading of the
+    paper's "PDHG following cuPDLP+", Section 4.1).
+
+    The candidate is the lower of KKT(current) and KKT(average); a tie keeps
+    the current iterate.  Three criteria, any of which restarts:
+      r1 (sufficient):  KKT(cand) <= beta_suff * KKT(last restart point)
+      r2 (necessary):   KKT(cand) <= beta_nec * KKT(last restart point) and
+                        KKT(cand) >  KKT(candidate of the previous evaluation)
+      r3 (artificial):  t >= beta_art * k  (t: iterations since the last
+                        restart, k: iterations in all)
+    Returns use_avg, k_cand, r1, r2, r3 and restart."""
+    opts = opts or Options()
+    use_avg = kkt_avg < kkt_cur
+    k_cand = kkt_avg if use_avg else kkt_cur
+    r1 = k_cand <= opts.beta_sufficient * kkt_last
+    r2 = (k_cand <= opts.beta_necessary * kkt_last) and (k_cand > kkt_prev)
+    r3 = t >= opts.beta_artificial * k
+    return dict(use_avg=bool(use_avg), k_cand=float(k_cand), r1=bool(r1), r2=bool(r2),
+                r3=bool(r3), restart=bool(r1 or r2 or r3))
+
+
+def advance_restart_kkts(kkt_last: float, k_cand: float, restart: bool):
+    """The two KKT references after an evaluation: the previous-candidate
+    value always becomes this evaluation's candidate; the last-restart value
+    becomes it only on a restart.  Returns (kkt_last, kkt_prev)."""
+    return (k_cand if restart else kkt_last), k_cand
+
+
+def omega_update(dx: float, dy: float, omega: float, theta: float = 0.5,
+                 min_dist: float = 1e-10) -> float:
+    """Primal weight at a restart: the geometric blend
+    exp(theta log(dy / dx) + (1 - theta) log omega) of the new ratio of the
+    dual to the primal distance moved since the last restart point and the
+    old weight; unchanged unless both distances exceed min_dist."""
+    if dx > min_dist and dy > min_dist:
+        return float(np.exp(theta * np.log(dy / dx) + (1.0 - theta) * np.log(omega)))
+    return float(omega)
+
+
+# ---------------------------------------------------------------------------
 # the restarted loop (a4-a8)
 # ---------------------------------------------------------------------------
 @dataclass
@@ -385,31 +430,24 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
             break  # k == max_iter: stop without applying the restart rule
         k_cur = kkt_error(At, b_t, c_t, st.x, st.y, st.omega)
         k_avg = kkt_error(At, b_t, c_t, st.x_avg, st.y_avg, st.omega)
-        use_avg = k_avg < k_cur
-        k_cand = k_avg if use_avg else k_cur
-        r1 = k_cand <= opts.beta_sufficient * st.kkt_last
-        r2 = (k_cand <= opts.beta_necessary * st.kkt_last) and (k_cand > st.kkt_prev)
-        r3 = st.t >= opts.beta_artificial * st.k
-        restart = r1 or r2 or r3
+        d = restart_decision(k_cur, k_avg, st.kkt_last, st.kkt_prev, st.t, st.k, opts)
+        use_avg, k_cand, restart = d["use_avg"], d["k_cand"], d["restart"]
         entry = dict(k=st.k, kkt_cur=k_cur, kkt_avg=k_avg, cand="average" if use_avg else "current",
-                     restart=restart, r1=r1, r2=r2, r3=r3, kkt_last=st.kkt_last,
-                     kkt_prev=st.kkt_prev, omega=st.omega)
-        st.kkt_prev = k_cand
+                     restart=restart, r1=d["r1"], r2=d["r2"], r3=d["r3"], kkt_last=st.kkt_last,
+                     kkt_prev=st.kkt_prev, omega=st.omega, t=st.t)
+        st.kkt_last, st.kkt_prev = advance_restart_kkts(st.kkt_last, k_cand, restart)
         if restart:
             xc = st.x_avg if use_avg else st.x
             yc = st.y_avg if use_avg else st.y
             dx = float(np.linalg.norm(xc - st.x_last))
             dy = float(np.linalg.norm(yc - st.y_last))
-            if dx > opts.omega_update_min and dy > opts.omega_update_min:
-                st.omega = float(np.exp(opts.theta * np.log(dy / dx)
-                                        + (1.0 - opts.theta) * np.log(st.omega)))
+            st.omega = omega_update(dx, dy, st.omega, opts.theta, opts.omega_update_min)
             st.x, st.y = xc.copy(), yc.copy()
             st.x_last, st.y_last = xc.copy(), yc.copy()
             st.x_avg = np.zeros_like(st.x)
             st.y_avg = np.zeros_like(st.y)
             st.t = 0
             st.restarts += 1
-            st.kkt_last = k_cand
             entry.update(dx=dx, dy=dy, omega_new=st.omega)
         log.append(entry)
         xs_out, ys_out = st.x, st.y

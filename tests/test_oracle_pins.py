@@ -371,3 +371,149 @@ def test_halpern_second_candidate_is_the_projected_pdhg_output():
     r2 = O.solve(lp, 1e-4, 200_000, opts=O.Options(method="halpern", reflection=1.0))
     if r2.chosen == "average":
         assert np.min(r2.x_scaled) >= 0.0
+
+
+# --------------------------------------------------------------- a8 restart rule and omega
+_RR = None
+
+
+def _rr():
+    global _RR
+    if _RR is None:
+        _RR = _load("restart_rule_cases.json")
+    return _RR
+
+
+def _decision_failures(decide):
+    """Names of the hand cases that `decide` (restart_decision's signature)
+    gets wrong."""
+    g = _rr()
+    opts = O.Options(**g["betas"])
+    bad = []
+    for c in g["decisions"]:
+        d = decide(c["kkt_cur"], c["kkt_avg"], c["kkt_last"], c["kkt_prev"], c["t"], c["k"], opts)
+        if any(d[key] != c[key] for key in ("use_avg", "k_cand", "r1", "r2", "r3", "restart")):
+            bad.append(c["name"])
+    return bad
+
+
+def _omega_failures(update):
+    bad = []
+    for c in _rr()["omega"]:
+        w = update(c["dx"], c["dy"], c["omega"], c["theta"], 1e-10)
+        if abs(w - c["omega_new"]) > 1e-14 * c["omega_new"]:
+            bad.append(c["name"])
+    return bad
+
+
+def test_restart_decision_hand_cases():
+    assert _decision_failures(O.restart_decision) == []
+
+
+def test_omega_update_hand_cases():
+    assert _omega_failures(O.omega_update) == []
+
+
+def test_restart_bookkeeping_trace_by_hand():
+    g = _rr()
+    tr = g["trace"]
+    opts = O.Options(**g["betas"])
+    last, prev = tr["start"]["kkt_last"], tr["start"]["kkt_prev"]
+    for e in tr["evals"]:
+        d = O.restart_decision(e["kkt_cur"], e["kkt_avg"], last, prev, e["t"], e["k"], opts)
+        for key in ("use_avg", "restart", "r1", "r2", "r3"):
+            assert d[key] == e[key], (e["k"], key)
+        last, prev = O.advance_restart_kkts(last, d["k_cand"], d["restart"])
+        assert (last, prev) == (e["kkt_last"], e["kkt_prev"]), e["k"]
+
+
+def _mutant_decision(kind):
+    def decide(kc, ka, kl, kp, t, k, opts):
+        use_avg = (ka <= kc) if kind == "tie_to_average" else (ka < kc)
+        cand = ka if use_avg else kc
+        r1 = cand <= opts.beta_sufficient * kl
+        if kind == "r2_against_last":
+            r2 = cand <= opts.beta_necessary * kl and cand > kl
+        elif kind == "r2_ge":
+            r2 = cand <= opts.beta_necessary * kl and cand >= kp
+        elif kind == "r2_against_current":
+            r2 = cand <= opts.beta_necessary * kl and kc > kp
+        else:
+            r2 = cand <= opts.beta_necessary * kl and cand > kp
+        r3 = (t > opts.beta_artificial * k) if kind == "r3_strict" else (t >= opts.beta_artificial * k)
+        if kind == "cand_is_current":
+            cand = kc
+            r1 = cand <= opts.beta_sufficient * kl
+        return dict(use_avg=use_avg, k_cand=cand, r1=r1, r2=r2, r3=r3, restart=r1 or r2 or r3)
+    return decide
+
+
+@pytest.mark.parametrize("kind", ["tie_to_average", "r2_against_last", "r2_ge", "r2_against_current",
+                                  "r3_strict", "cand_is_current"])
+def test_restart_pins_catch_planted_slips(kind):
+    """Each plausible slip in the rule, planted in a copy on the CPU, fails a
+    named hand case."""
+    assert _decision_failures(_mutant_decision(kind)) != []
+
+
+@pytest.mark.parametrize("kind", ["swap_dx_dy", "swap_theta", "no_old_weight", "guard_ge"])
+def test_omega_pins_catch_planted_slips(kind):
+    def update(dx, dy, w, theta, mn):
+        if kind == "guard_ge":
+            ok = dx >= mn and dy >= mn
+        else:
+            ok = dx > mn and dy > mn
+        if not ok:
+            return w
+        if kind == "swap_dx_dy":
+            dx, dy = dy, dx
+        if kind == "swap_theta":
+            theta = 1.0 - theta
+        if kind == "no_old_weight":
+            return float(np.exp(theta * np.log(dy / dx)))
+        return float(np.exp(theta * np.log(dy / dx) + (1.0 - theta) * np.log(w)))
+    assert _omega_failures(update) != []
+
+
+def test_solve_applies_the_rule_it_logs():
+    """The loop feeds the rule the right references: every logged evaluation
+    equals restart_decision on the logged inputs, kkt_last / kkt_prev move as
+    the bookkeeping says, and omega moves by omega_update on the logged
+    distances (wiring check of the loop around the pinned functions)."""
+    lp = lpgen.planted_lp(m=60, n=150, nnz_per_col=4, seed=5)
+    res = O.solve(lp, eps_rel=1e-7, max_iter=64 * 40)
+    opts = O.Options()
+    assert len(res.log) >= 5 and any(e["restart"] for e in res.log)
+    assert any(e["restart"] and not e["r3"] for e in res.log)
+    for e, nxt in zip(res.log, res.log[1:] + [None]):
+        d = O.restart_decision(e["kkt_cur"], e["kkt_avg"], e["kkt_last"], e["kkt_prev"],
+                               e["t"], e["k"], opts)
+        assert (d["restart"], d["r1"], d["r2"], d["r3"]) == (e["restart"], e["r1"], e["r2"], e["r3"])
+        assert e["cand"] == ("average" if d["use_avg"] else "current")
+        last, prev = O.advance_restart_kkts(e["kkt_last"], d["k_cand"], d["restart"])
+        if e["restart"]:
+            w = O.omega_update(e["dx"], e["dy"], e["omega"], opts.theta, opts.omega_update_min)
+            assert e["omega_new"] == w
+        if nxt is not None:
+            assert (nxt["kkt_last"], nxt["kkt_prev"]) == (last, prev)
+            assert nxt["omega"] == (e["omega_new"] if e["restart"] else e["omega"])
+            assert nxt["t"] == (nxt["k"] - e["k"] if e["restart"] else e["t"] + nxt["k"] - e["k"])
+
+
+@pytest.mark.parametrize("kind", ["prev_only_on_restart", "last_always", "prev_is_current"])
+def test_bookkeeping_trace_catches_planted_slips(kind):
+    g = _rr()
+    tr = g["trace"]
+    opts = O.Options(**g["betas"])
+    last, prev = tr["start"]["kkt_last"], tr["start"]["kkt_prev"]
+    wrong = False
+    for e in tr["evals"]:
+        d = O.restart_decision(e["kkt_cur"], e["kkt_avg"], last, prev, e["t"], e["k"], opts)
+        if kind == "prev_only_on_restart":
+            last, prev = (d["k_cand"], d["k_cand"]) if d["restart"] else (last, prev)
+        elif kind == "last_always":
+            last, prev = d["k_cand"], d["k_cand"]
+        else:
+            last, prev = (d["k_cand"] if d["restart"] else last), e["kkt_cur"]
+        wrong |= (last, prev) != (e["kkt_last"], e["kkt_prev"])
+    assert wrong
