@@ -231,42 +231,45 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(precision, device_io=True, timing=False, outs=None):
-        src = devt if device_io else pinned
-        s = pdhg.Solver(m, n, src["row_ptr"], src["col"], src["val"], src["b"], src["c"],
-                        precision=precision, device_io=device_io, stream=stream.cuda_stream,
-                        kernel_timing=timing, method=args.method, spmv_layout=args.layout)
-        st = s.solve(EPS, args.max_iter)
-        g = s.get(out=outs[0] if outs else None)
-        w = s.warmstart_point(unscaled=True, out=outs[1] if outs else None)
-        return s, st, g, w
-
-    def run_steps(precision, k, w, device_io=True, timing=False):
+    def run_steps(precision, k, w, device_io=True):
+        """k timed steps after w untimed ones; each step's GPU timeline split
+        by events on the solver's stream: create | solve | get + Algorithm 1."""
         outs = None
         if not device_io:
             mk = lambda L: torch.empty(L, dtype=torch.float64).pin_memory()
             outs = ((mk(n), mk(m), mk(n)), (mk(n), mk(m), mk(n)))
+        src = devt if device_io else pinned
         rec = []
         for i in range(w + k):
             with torch.cuda.stream(stream):
                 flush.fill_(float(i))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             stream.synchronize()
-            e0.record(stream)
-            s, st, g, wp = step(precision, device_io, timing, outs)
-            e1.record(stream)
+            ev[0].record(stream)
+            s = pdhg.Solver(m, n, src["row_ptr"], src["col"], src["val"], src["b"], src["c"],
+                            precision=precision, device_io=device_io, stream=stream.cuda_stream,
+                            method=args.method, spmv_layout=args.layout)
+            ev[1].record(stream)
+            st = s.solve(EPS, args.max_iter)
+            ev[2].record(stream)
+            g = s.get(out=outs[0] if outs else None)
+            s.warmstart_point(unscaled=True, out=outs[1] if outs else None)
+            ev[3].record(stream)
             stream.synchronize()
-            info = s.info(violation=False)
-            kt = s.kernel_timing_parts() if timing else None
+            # outside the timed region: counters, the Section 4.3 violation
+            info = s.info(violation=True)
             launches = s.launch_count()
+            checks = s.fp64_checks()
             sched = s.schedule()
             layout = s.layout()
             s.close()
             if i >= w:
-                rec.append(dict(ms=e0.elapsed_time(e1), iters=info["iters"], status=st,
-                                r_P=g["r_P"], r_D=g["r_D"], gap=g["gap"], kt=kt,
-                                launches=launches, sched=sched, layout=layout,
+                rec.append(dict(ms=ev[0].elapsed_time(ev[3]), create_ms=ev[0].elapsed_time(ev[1]),
+                                solve_ms=ev[1].elapsed_time(ev[2]),
+                                get_ms=ev[2].elapsed_time(ev[3]), iters=info["iters"], status=st,
+                                r_P=g["r_P"], r_D=g["r_D"], gap=g["gap"],
+                                max_violation=info["max_violation"], launches=launches,
+                                fp64_checks=checks, sched=sched, layout=layout,
                                 obj=float(torch.dot(torch.as_tensor(g["x"]).to(dev),
                                                     devt["c"]).item())))
         return rec
@@ -275,12 +278,13 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        rec = run_steps(args.precision, args.steps, args.warmup, timing=True)
+        rec = run_steps(args.precision, args.steps, args.warmup)
         torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     total_ms = sum(r["ms"] for r in rec)
     total_it = sum(r["iters"] for r in rec)
+    solve_ms = sum(r["solve_ms"] for r in rec)
     if ws > 1:
         total_ms, total_it_all = reduce_over_ranks(total_ms, total_it, dev)
     else:
@@ -299,26 +303,36 @@ def run_ours(args):
     if args.fp64_steps > 0 and args.precision != "fp64":
         r64 = run_steps("fp64", args.fp64_steps, 1)
         fp64 = dict(time_to_eps_s=float(np.mean([r["ms"] for r in r64]) / 1e3),
+                    create_ms=float(np.mean([r["create_ms"] for r in r64])),
+                    solve_ms=float(np.mean([r["solve_ms"] for r in r64])),
                     iters=int(np.mean([r["iters"] for r in r64])),
                     iter_per_s=sum(r["iters"] for r in r64) / (sum(r["ms"] for r in r64) / 1e3),
-                    status=[r["status"] for r in r64])
+                    solve_iter_per_s=sum(r["iters"] for r in r64) /
+                    (sum(r["solve_ms"] for r in r64) / 1e3),
+                    status=[pdhg.STATUS_NAMES.get(r["status"], r["status"]) for r in r64],
+                    max_violation=max(r["max_violation"] for r in r64), objective=r64[-1]["obj"])
 
-    # roofline of the dominant half-step (sampled CUDA-event durations).  On
-    # the CSR tiles a half-step is one fused kernel; on the column panels it
-    # is the panel SpMV plus the row pass, and the pair is the unit whose
+    # roofline of the dominant half-step: back-to-back launches of each
+    # half-step on a solved iterate of the same LP (pdhg_time_kernels: CUDA
+    # events around the run, none between launches), after the timed steps.
+    # On the CSR tiles a half-step is one fused kernel; on the column panels
+    # it is the panel SpMV plus the row pass, and the pair is the unit whose
     # algorithmic bytes are counted (the panel partial sums are not).
     s_bytes = 4 if args.precision == "fp32" else 8
     ab = algorithmic_bytes(m, n, nnz, s_bytes)
-    ns = sum(r["kt"]["samples"] for r in rec)
-
-    def mean_part(key):
-        return sum(r["kt"][key] * r["kt"]["samples"] for r in rec) / max(ns, 1)
-
-    lay = rec[0]["layout"]
+    with torch.cuda.stream(stream):
+        sk = pdhg.Solver(m, n, devt["row_ptr"], devt["col"], devt["val"], devt["b"], devt["c"],
+                         precision=args.precision, device_io=True, stream=stream.cuda_stream,
+                         method=args.method, spmv_layout=args.layout)
+        sk.solve(EPS, args.max_iter)
+        kt = sk.time_kernels(args.kernel_reps)
+        gf = {"dual": sk.gather_floor(True, 20), "primal": sk.gather_floor(False, 20)}
+        lay = sk.layout()
+        sched = sk.schedule()
+        sk.close()
     on_panels = {"primal": lay["at"]["panels"] > 0, "dual": lay["a"]["panels"] > 0}
-    parts = {"primal": (mean_part("primal_spmv_ms"), mean_part("primal_rows_ms")),
-             "dual": (mean_part("dual_spmv_ms"), mean_part("dual_rows_ms"))}
-    half = {h: parts[h][0] + (parts[h][1] if on_panels[h] else 0.0) for h in parts}
+    half = {"primal": kt["primal_ms"], "dual": kt["dual_ms"]}
+    spmv = {"primal": kt["primal_spmv_ms"], "dual": kt["dual_spmv_ms"]}
     names = {"primal": ("k_panel_spmv + k_panel_primal" if on_panels["primal"] else "k_primal"),
              "dual": ("k_panel_spmv + k_panel_dual" if on_panels["dual"] else "k_dual")}
     dom = "primal" if half["primal"] >= half["dual"] else "dual"
@@ -326,7 +340,10 @@ def run_ours(args):
     dur = half[dom]
     peak, peak_src = peaks()
     ach = ab[dom] / (dur / 1e3) / 1e9 if dur > 0 else 0.0
-    variant = rec[0]["sched"]["at_variant" if dom == "primal" else "a_variant"]
+    variant = sched["at_variant" if dom == "primal" else "a_variant"]
+    it_bytes = ab["primal"] + ab["dual"]
+    it_ms = kt["iteration_ms"]
+    solve_it_ms = solve_ms / max(total_it, 1)
     roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4),
                 "traffic": ncu_traffic(("panel_" + dom) if on_panels[dom] else
@@ -336,20 +353,22 @@ def run_ours(args):
                 "kernel": names[dom], "half_step": dom,
                 "layout": "column panels" if on_panels[dom] else "CSR tiles",
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": ab[dom],
-                "mean_launch_ms": round(dur, 5), "samples": ns,
-                "kernels_ms": {"spmv_or_fused": round(parts[dom][0], 5),
-                               "row_pass": round(parts[dom][1], 5) if on_panels[dom] else None},
+                "mean_launch_ms": round(dur, 5),
+                "timing": f"pdhg_time_kernels: {args.kernel_reps} back-to-back launches of each "
+                          "half-step on a solved iterate of the same LP, CUDA events on the "
+                          "launching stream around the run",
+                "kernels_ms": {"spmv_or_fused": round(spmv[dom] if on_panels[dom] else dur, 5),
+                               "row_pass": round(dur - spmv[dom], 5) if on_panels[dom] else None},
                 "other": {"kernel": names[oth], "mean_launch_ms": round(half[oth], 5),
-                          "achieved_gbs": round(ab[oth] / (max(half[oth], 1e-9) / 1e3) / 1e9, 1)},
-                "note": "each sampled interval is bracketed by CUDA events recorded in the "
-                        "iteration's graph; an empty interval reads about 2 us"}
-    # the second bound: the same nonzeros' loads and random gathers without the
-    # row logic (pdhg_gather_floor), timed on a fresh context after the steps
-    with torch.cuda.stream(stream):
-        sf = pdhg.Solver(m, n, devt["row_ptr"], devt["col"], devt["val"], devt["b"], devt["c"],
-                         precision=args.precision, device_io=True, stream=stream.cuda_stream)
-        gf = {"dual": sf.gather_floor(True, 20), "primal": sf.gather_floor(False, 20)}
-        sf.close()
+                          "achieved_gbs": round(ab[oth] / (max(half[oth], 1e-9) / 1e3) / 1e9, 1),
+                          "spmv_ms": round(spmv[oth], 5) if on_panels[oth] else None},
+                "iteration": {"algorithmic_bytes": it_bytes, "ms": round(it_ms, 5),
+                              "achieved_gbs": round(it_bytes / (it_ms / 1e3) / 1e9, 1) if it_ms else None,
+                              "frac": round(it_bytes / (it_ms / 1e3) / 1e9 / peak, 4) if it_ms else None,
+                              "in_solve_ms": round(solve_it_ms, 5),
+                              "in_solve_frac": round(it_bytes / (solve_it_ms / 1e3) / 1e9 / peak, 4),
+                              "note": "in_solve: the timed steps' pdhg_solve time / iterations "
+                                      "(evaluations, restarts and float64 checks included)"}}
     roofline["gather_floor"] = {
         "what": "mean ms of a pass over the same nonzeros keeping only the index/value loads, "
                 "the random gathers and one FMA each (no row logic, scan or epilogue)",
@@ -372,12 +391,20 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[args.workload], "precision": args.precision +
                        ("_mixed (f64 norms, gap, restart rule, step/weight updates)" if args.precision == "fp32" else ""),
                        "eps_rel": EPS, "method": args.method, "layout": args.layout,
-                       "step": "create + solve to eps + get + warmstart_point",
+                       "step": "create + solve to eps + get + warmstart_point (create and "
+                               "solve also reported apart)",
                        "l2": "flushed between steps (512 MiB write), inputs resident in HBM",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "schedule": rec[0]["sched"]},
             "time_to_eps_s": round(ms_step / 1e3, 5),
+            "create_ms": round(float(np.mean([r["create_ms"] for r in rec])), 3),
+            "solve_ms": round(solve_ms / max(len(rec), 1), 3),
+            "solve_iter_per_s": round(total_it / (solve_ms / 1e3), 2),
+            "get_and_warmstart_ms": round(float(np.mean([r["get_ms"] for r in rec])), 3),
             "iters_to_eps": int(np.mean([r["iters"] for r in rec])),
+            "max_violation": max(r["max_violation"] for r in rec),
+            "fp64_checks": {"run": int(sum(r["fp64_checks"][0] for r in rec)),
+                            "rejected": int(sum(r["fp64_checks"][1] for r in rec))},
             "status": [pdhg.STATUS_NAMES.get(r["status"], r["status"]) for r in rec],
             "kkt_at_exit": {"r_P": rec[-1]["r_P"], "r_D": rec[-1]["r_D"], "gap": rec[-1]["gap"]},
             "roofline": roofline,
@@ -390,9 +417,14 @@ def run_ours(args):
         if lp.x_star is not None:
             obj = float(lp.c @ lp.x_star)
             line["objective_rel_err_vs_planted"] = abs(rec[-1]["obj"] - obj) / (1 + abs(obj))
+            if fp64:
+                fp64["objective_rel_err_vs_planted"] = abs(fp64["objective"] - obj) / (1 + abs(obj))
         if fp64:
             line["fp64"] = fp64
+            line["objective_rel_err_vs_fp64"] = (abs(rec[-1]["obj"] - fp64["objective"]) /
+                                                 (1 + abs(fp64["objective"])))
             line["fp32_vs_fp64_time_speedup"] = round(fp64["time_to_eps_s"] / (ms_step / 1e3), 3)
+            line["fp32_vs_fp64_solve_speedup"] = round(fp64["solve_ms"] / (solve_ms / max(len(rec), 1)), 3)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -695,6 +727,22 @@ def run_hybrid(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """A short fixed run for profilers (ncu): one context on --workload, then
+    --profile-run iterations with eps_rel = 0 (no test can end it early).
+    Prints the iterations done and the layout of each half-step."""
+    from paper_2603_03150_gb300 import build as B
+    from paper_2603_03150_gb300 import pdhg
+    B.build()
+    lp = make_lp(args.workload)
+    layout = args.layout
+    with pdhg.Solver.from_lp(lp, precision=args.precision, spmv_layout=layout,
+                             method=args.method) as s:
+        s.solve(0.0, args.profile_run)
+        print(json.dumps({"iters": s.info(violation=False)["iters"], "layout": s.layout(),
+                          "schedule": s.schedule(), "launches": s.launch_count()}), flush=True)
+
+
 def cpu_baseline(lp, iters, method="averaged"):
     """The oracle as it stands, timed on this host: its set-up once (timed
     apart), then `iters` PDHG iterations (steady-state iterations per second)."""
@@ -767,17 +815,24 @@ def main():
                     help="PDHG iteration: restarted averaged (default) or reflected Halpern")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=128)
+    ap.add_argument("--kernel-reps", type=int, default=50,
+                    help="back-to-back launches per half-step for the roofline timing")
     ap.add_argument("--ref-iters", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER,
                     help="iteration cap per solve (profiling runs use a small cap)")
+    ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS",
+                    help="profiling mode: ITERS iterations on --workload with eps_rel = 0, "
+                         "no timing (for ncu)")
     ap.add_argument("--eps-sweep", action="store_true",
                     help="tolerance sweep 1e-4 / 1e-6 / 1e-8 on --workload (FP64 and FP32-mixed)")
     args = ap.parse_args()
     args.precision_set = any(a.startswith("--precision") for a in sys.argv[1:])
-    if args.warmup < 3:
+    if args.warmup < 3 and args.profile_run == 0:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.profile_run > 0:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "hybrid":
         run_hybrid(args)

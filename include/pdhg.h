@@ -104,6 +104,14 @@ typedef struct pdhg_options {
                               (about 49k columns); > 0: at most this many
                               columns per panel (rounded down to a multiple of
                               8, at least 8)                                   */
+  double fp32_screen;      /* PDHG_FP32_MIXED: the Section 2 test evaluated on
+                              the float32 caches is a screen that passes at
+                              eps_rel * fp32_screen (default 1, at most 1e6);
+                              the screened candidate is then re-evaluated with
+                              every product recomputed in float64, and only
+                              that test at eps_rel ends the solve (a rejected
+                              candidate continues: the restart rule of that
+                              evaluation is applied as usual)                  */
 } pdhg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -127,7 +135,12 @@ pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const int32_t* row
 /* Run restarted PDHG from the context's current state until the Section 2
  * test holds with eps = eps_rel (evaluated every F iterations, on the current
  * iterate first, then the running average) or the cumulative iteration count
- * reaches max_iter.  Returns PDHG_CONVERGED, PDHG_MAX_ITER or an error.  */
+ * reaches max_iter.  Returns PDHG_CONVERGED, PDHG_MAX_ITER or an error.
+ * PDHG_FP32_MIXED: the test on the float32 caches only screens; the solve
+ * converges when the screened iterate passes the test in float64 (x~, y~
+ * widened to float64, A~x~ and A~^T y~ recomputed from the float64 scaled
+ * matrices), so a converged float32-mixed solve meets the test at eps_rel
+ * exactly as pdhg_get reports it.  */
 pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_iter);
 
 /* The returned iterate (the one that passed the test, else the current one)
@@ -135,6 +148,12 @@ pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_iter);
  * ||r_P||_2, ||r_D||_2, |c^T x - b^T y|, all evaluated in float64.  */
 pdhg_status pdhg_get(pdhg_ctx* ctx, double* x, double* y, double* z, double* r_P,
                      double* r_D, double* gap);
+
+/* Float64 checks of float32-mixed candidates in the last solve (single LP
+ * or summed over a batch): how many screened candidates were re-evaluated
+ * in float64 and how many of them failed the Section 2 test there and were
+ * iterated on.  Float64 contexts report 0, 0.  */
+pdhg_status pdhg_get_fp64_checks(pdhg_ctx* ctx, int64_t* checks, int64_t* rejects);
 
 /* Iterations done, restarts taken, the Section 4.3 maximum violation
  * max(||r_P||_inf, ||r_D||_inf, x^T z / (1 + |c^T x|)) of the returned
@@ -212,6 +231,18 @@ pdhg_status pdhg_get_kernel_timing(pdhg_ctx* ctx, double* primal_ms, double* dua
  * reads 0); on the column panels, the panel SpMV and the row pass that adds
  * the panel sums and applies the step.  */
 pdhg_status pdhg_get_kernel_timing_parts(pdhg_ctx* ctx, double* ms, int64_t* samples);
+
+/* Mean duration in ms of `reps` back-to-back launches (after 3 untimed) of,
+ * ms[5] (HOST): {0: the primal half-step (A~^T y~ and the projected primal
+ * step), 1: the dual half-step (A~ x~+ and the dual step), 2: one iteration
+ * (both in turn), 3: the column-panel SpMV kernel of the primal half-step
+ * alone, 4: that of the dual half-step (3, 4: 0 on the CSR tiles, where a
+ * half-step is one fused kernel)}, timed with CUDA events on the context's
+ * stream on its current iterate.  Launches are back to back as in a solve
+ * (programmatic dependent launch), with no event between them.  The solver
+ * state is saved to a temporary device buffer first and restored after, so
+ * a solve continues as if the call had not happened.  Single-LP contexts.  */
+pdhg_status pdhg_time_kernels(pdhg_ctx* ctx, int32_t reps, double* ms);
 
 /* Tile schedule picked for A (dual kernel) and A^T (primal kernel): nonzeros
  * per tile (at most), threads per block, tiles, and the SpMV variant (8, 16,
@@ -291,13 +322,12 @@ pdhg_status pdhg_batch_adjoint(pdhg_ctx* ctx, const double* grad_x, double* grad
                                double* grad_c, double cg_tol, int32_t cg_max_iter,
                                int32_t* lp_cg_iters);
 
-/* Algorithm 1's centered start point (as pdhg_warmstart_point, scaled
- * output) for caller-provided DEVICE vectors, allocating no device memory.
- * The paper has no counterpart of this entry point: it exists for callers
- * that cannot call cudaMalloc -- code that runs while its stream is being
- * captured into a CUDA graph (allocation is not capturable), an
- * interior-point solver that owns a fixed device memory pool, or a thread
- * that must not take the allocator's locks.
+/* The scaled start point of pdhg_warmstart_point, computed for caller-provided
+ * DEVICE vectors with no device allocation by the library.  The paper has no
+ * counterpart of this entry point.  It exists for callers that cannot call
+ * cudaMalloc: an interior-point solver that owns a fixed device memory pool
+ * and must not grow it, or a host thread that must not take the device
+ * allocator's locks (for example a latency-bound solver loop).
  *  n              entries, 1 <= n <= 8,388,608 (larger n -> PDHG_INVALID_ARG;
  *                 the static scratch holds 4096 partial sums of 2048 entries)
  *  x, z           device float64[n]: the PDHG x and z of the scaled LP
@@ -308,10 +338,13 @@ pdhg_status pdhg_batch_adjoint(pdhg_ctx* ctx, const double* grad_x, double* grad
  * (32 KB, held until the process exits), shared by every call: calls whose
  * work overlaps on the GPU race and must be serialised by the caller (for
  * example by using one stream).  Each call writes every scratch slot it
- * reads, so nothing needs clearing between calls.  The first call on a
- * device looks up the array's device address with that device current;
- * make that first call before any stream capture.  The call is
- * asynchronous: results are ready when `stream` reaches it.  */
+ * reads before reading it, so nothing needs clearing between calls.  The
+ * first call on a device looks up the array's device address with that
+ * device current and caches it for the process; make that first call
+ * before any stream capture.  The cached address belongs to the device's
+ * primary context: after cudaDeviceReset the library must not be used
+ * again in the process.  The call is asynchronous: results are ready when
+ * `stream` reaches it.  */
 pdhg_status pdhg_centered_point_noalloc(int32_t n, const double* x, const double* z,
                                         double mu_min, double delta_max, double alpha_min,
                                         double* x_out, double* z_out, double* mu_target,

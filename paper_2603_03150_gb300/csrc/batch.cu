@@ -425,14 +425,17 @@ __global__ void k_binit(Scalars* sc, const PowerState* ps, const int64_t* m_off,
 // float64 report and Algorithm 1 per LP
 // ---------------------------------------------------------------------------
 // the returned iterate of each LP (average if that passed the test) in float64
+// checking = true: only the LPs with a pending float64 check, their screened
+// candidate
 template <typename T>
 __global__ void k_bchoose(SchedView Sn, SchedView Sm, const Scalars* sc, const T* x, const T* x_avg,
-                          const T* y, const T* y_avg, double* xs, double* ys) {
+                          const T* y, const T* y_avg, double* xs, double* ys, bool checking) {
   for (int t = blockIdx.x; t < Sn.ntiles; t += gridDim.x) {
     const Tile tl = Sn.tiles[t];
     if (tl.split >= 0 && tl.part != 0) continue;
     const Scalars& s = sc[tl.lp];
-    const bool avg = s.done && s.status == 0 && s.chosen_avg;
+    if (checking && !s.verify) continue;
+    const bool avg = checking ? s.verify_avg != 0 : (s.done && s.status == 0 && s.chosen_avg);
     for (int j = tl.row_begin + threadIdx.x; j < tl.row_end; j += blockDim.x)
       xs[j] = (double)(avg ? x_avg[j] : x[j]);
   }
@@ -440,26 +443,29 @@ __global__ void k_bchoose(SchedView Sn, SchedView Sm, const Scalars* sc, const T
     const Tile tl = Sm.tiles[t];
     if (tl.split >= 0 && tl.part != 0) continue;
     const Scalars& s = sc[tl.lp];
-    const bool avg = s.done && s.status == 0 && s.chosen_avg;
+    if (checking && !s.verify) continue;
+    const bool avg = checking ? s.verify_avg != 0 : (s.done && s.status == 0 && s.chosen_avg);
     for (int i = tl.row_begin + threadIdx.x; i < tl.row_end; i += blockDim.x)
       ys[i] = (double)(avg ? y_avg[i] : y[i]);
   }
 }
 
+// gate (optional): only the tiles of LPs with a pending float64 check
 template <int BLOCK>
 struct BRepNEpi {
   const double *x_s, *c_t, *D_c;
   double *x_out, *z_out, *rec, *red;
+  const Scalars* gate;
   double u2, s3, xz, inf;
-  __device__ __forceinline__ bool begin_tile(const Tile&) {
+  __device__ __forceinline__ bool begin_tile(const Tile& tl) {
     u2 = s3 = xz = inf = 0.0;
-    return true;
+    return !gate || gate[tl.lp].verify;
   }
   __device__ __forceinline__ void row(int j, const double (&s)[1], int) {
     const double d = c_t[j] - s[0];
     const double zs = fmax(0.0, d), rd = fmin(0.0, d) / D_c[j];
-    x_out[j] = D_c[j] * x_s[j];
-    z_out[j] = zs / D_c[j];
+    if (x_out) x_out[j] = D_c[j] * x_s[j];
+    if (z_out) z_out[j] = zs / D_c[j];
     u2 += rd * rd;
     s3 += c_t[j] * x_s[j];
     xz += x_s[j] * zs;
@@ -490,14 +496,15 @@ template <int BLOCK>
 struct BRepMEpi {
   const double *y_s, *b_t, *D_r;
   double *y_out, *rec, *red;
+  const Scalars* gate;
   double u1, s4, inf;
-  __device__ __forceinline__ bool begin_tile(const Tile&) {
+  __device__ __forceinline__ bool begin_tile(const Tile& tl) {
     u1 = s4 = inf = 0.0;
-    return true;
+    return !gate || gate[tl.lp].verify;
   }
   __device__ __forceinline__ void row(int i, const double (&s)[1], int) {
     const double rp = (b_t[i] - s[0]) / D_r[i];
-    y_out[i] = D_r[i] * y_s[i];
+    if (y_out) y_out[i] = D_r[i] * y_s[i];
     u1 += rp * rp;
     s4 += b_t[i] * y_s[i];
     inf = fmax(inf, fabs(rp));
@@ -528,10 +535,10 @@ __global__ void __launch_bounds__(BLOCK) k_brep_n(SchedView S, const int32_t* rp
                                                  const double* val, const double* x_s,
                                                  const double* y_s, const double* c_t,
                                                  const double* D_c, double* x_out, double* z_out,
-                                                 double* rec) {
+                                                 double* rec, const Scalars* gate) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[3 * (BLOCK / 32)];
-  BRepNEpi<BLOCK> epi{x_s, c_t, D_c, x_out, z_out, rec, red, 0, 0, 0, 0};
+  BRepNEpi<BLOCK> epi{x_s, c_t, D_c, x_out, z_out, rec, red, gate, 0, 0, 0, 0};
   Gather<double, 1> g{{y_s}};
   run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
 }
@@ -540,10 +547,11 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_brep_m(SchedView S, const int32_t* rp, const int32_t* col,
                                                  const double* val, const double* x_s,
                                                  const double* y_s, const double* b_t,
-                                                 const double* D_r, double* y_out, double* rec) {
+                                                 const double* D_r, double* y_out, double* rec,
+                                                 const Scalars* gate) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[2 * (BLOCK / 32)];
-  BRepMEpi<BLOCK> epi{y_s, b_t, D_r, y_out, rec, red, 0, 0, 0};
+  BRepMEpi<BLOCK> epi{y_s, b_t, D_r, y_out, rec, red, gate, 0, 0, 0};
   Gather<double, 1> g{{x_s}};
   run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
 }
@@ -573,6 +581,27 @@ __global__ void k_brep_final(const double* rec_n, const int32_t* lp_n, const dou
     o[5] = s4;
     o[6] = xz;
     o[7] = 0.0;
+  }
+}
+
+// Float64 check of each LP whose screen passed: the Section 2 test at eps on
+// its report records; an LP that passes is finished (one fewer active LP)
+__global__ void k_bfp64_final(const double* rec_n, const int32_t* lp_n, const double* rec_m,
+                              const int32_t* lp_m, int count, Scalars* sc, int32_t* ctl) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
+    Scalars& s = sc[l];
+    if (!s.verify) continue;
+    double u2 = 0, s3 = 0, u1 = 0, s4 = 0;
+    for (int t = lp_n[l]; t < lp_n[l + 1]; ++t) {
+      u2 += rec_n[(size_t)t * kRecR];
+      s3 += rec_n[(size_t)t * kRecR + 1];
+    }
+    for (int t = lp_m[l]; t < lp_m[l + 1]; ++t) {
+      u1 += rec_m[(size_t)t * kRecR];
+      s4 += rec_m[(size_t)t * kRecR + 1];
+    }
+    eval_fp64_check(s, u1, u2, s3, s4, nullptr, nullptr, nullptr);
+    if (s.done) atomicSub(ctl, 1);
   }
 }
 
@@ -767,6 +796,22 @@ static void enqueue_bchunk(pdhg_ctx* ctx, int len) {
   PDHG_DISPATCH_E(B.it.t_sched.e,
                    (k_beval<T, kBlock, E_><<<ctx->l_eval.grid, kBlock, ctx->l_eval.smem,
                                               ctx->stream>>>(B, len)));
+  if constexpr (sizeof(T) == 4) {
+    // float64 check of the LPs whose screen passed
+    k_bchoose<T><<<ctx->restart_grid, 256, 0, ctx->stream>>>(
+        ctx->st8.view, ctx->sa8.view, ctx->sc, B.it.x, B.it.x_avg, B.it.y, B.it.y_avg, ctx->xs64,
+        ctx->ys64, true);
+    k_brep_n<kBlock><<<ctx->l_t64.grid, kBlock, ctx->l_t64.smem, ctx->stream>>>(
+        ctx->st8.view, ctx->t_rp, ctx->t_col, ctx->t_val64, ctx->xs64, ctx->ys64, ctx->c_t64,
+        ctx->D_c, nullptr, nullptr, ctx->rec_t, ctx->sc);
+    k_brep_m<kBlock><<<ctx->l_a64.grid, kBlock, ctx->l_a64.smem, ctx->stream>>>(
+        ctx->sa8.view, ctx->a_rp, ctx->a_col, ctx->a_val64, ctx->xs64, ctx->ys64, ctx->b_t64,
+        ctx->D_r, nullptr, ctx->rec_a, ctx->sc);
+    k_bfp64_final<<<(ctx->count + 255) / 256, 256, 0, ctx->stream>>>(
+        ctx->rec_t, ctx->lp_t8_tiles, ctx->rec_a, ctx->lp_a8_tiles, ctx->count, ctx->sc,
+        ctx->active);
+    ctx->launches += kFp64CheckLaunches;
+  }
   k_brestart<T><<<ctx->restart_grid, 256, 0, ctx->stream>>>(B);
 }
 
@@ -1103,9 +1148,9 @@ extern "C" pdhg_status pdhg_batch_create(pdhg_ctx** out, int32_t count, const in
     pdhg_default_options(&ctx->opt);
   if (ctx->opt.eval_freq < 1 ||
       (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED) ||
-      ctx->opt.method != 0) {
-    set_error("invalid options (eval_freq >= 1, precision 0/1, method 0: batched solves use "
-              "the averaged iteration)");
+      ctx->opt.method != 0 || !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6)) {
+    set_error("invalid options (eval_freq >= 1, precision 0/1, 1 <= fp32_screen <= 1e6, "
+              "method 0: batched solves use the averaged iteration)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }
@@ -1169,6 +1214,11 @@ extern "C" pdhg_status pdhg_batch_solve(pdhg_ctx* ctx, double eps_rel, int64_t m
     s.status = PDHG_MAX_ITER;
     s.restart_pending = 0;
     s.k = k;
+    s.fp64_check = ctx->mixed ? 1 : 0;
+    s.screen = ctx->opt.fp32_screen;
+    s.verify = 0;
+    s.checks = 0;
+    s.rejects = 0;
   }
   CK(cudaMemcpyAsync(ctx->sc, hs.data(), sizeof(Scalars) * count, cudaMemcpyHostToDevice,
                      ctx->stream));
@@ -1191,7 +1241,7 @@ extern "C" pdhg_status pdhg_batch_solve(pdhg_ctx* ctx, double eps_rel, int64_t m
     const int len = (int)(next - k);
     if (len == F && ctx->opt.use_graphs) {
       CK(cudaGraphLaunch(ctx->chunk_exec[slot], ctx->stream));
-      ctx->launches += 2 * F + 2;
+      ctx->launches += 2 * F + 2 + (ctx->mixed ? kFp64CheckLaunches : 0);
     } else {
       enqueue_batch_chunk(ctx, len);
       CK(cudaGetLastError());
@@ -1227,11 +1277,11 @@ static pdhg_status batch_returned64(pdhg_ctx* ctx) {
   if (ctx->mixed)
     k_bchoose<float><<<ctx->restart_grid, 256, 0, ctx->stream>>>(
         ctx->st.view, ctx->sa.view, ctx->sc, (const float*)ctx->x, (const float*)ctx->x_avg,
-        (const float*)ctx->y, (const float*)ctx->y_avg, ctx->xs64, ctx->ys64);
+        (const float*)ctx->y, (const float*)ctx->y_avg, ctx->xs64, ctx->ys64, false);
   else
     k_bchoose<double><<<ctx->restart_grid, 256, 0, ctx->stream>>>(
         ctx->st.view, ctx->sa.view, ctx->sc, (const double*)ctx->x, (const double*)ctx->x_avg,
-        (const double*)ctx->y, (const double*)ctx->y_avg, ctx->xs64, ctx->ys64);
+        (const double*)ctx->y, (const double*)ctx->y_avg, ctx->xs64, ctx->ys64, false);
   ctx->launches += 1;
   CK(cudaGetLastError());
   return PDHG_OK;
@@ -1251,10 +1301,10 @@ extern "C" pdhg_status pdhg_batch_get(pdhg_ctx* ctx, double* x, double* y, doubl
   CKS(batch_returned64(ctx));
   k_brep_n<kBlock><<<ctx->l_t64.grid, kBlock, ctx->l_t64.smem, ctx->stream>>>(
       ctx->st8.view, ctx->t_rp, ctx->t_col, ctx->t_val64, ctx->xs64, ctx->ys64, ctx->c_t64,
-      ctx->D_c, ctx->out_n1, ctx->out_n2, ctx->rec_t);
+      ctx->D_c, ctx->out_n1, ctx->out_n2, ctx->rec_t, nullptr);
   k_brep_m<kBlock><<<ctx->l_a64.grid, kBlock, ctx->l_a64.smem, ctx->stream>>>(
       ctx->sa8.view, ctx->a_rp, ctx->a_col, ctx->a_val64, ctx->xs64, ctx->ys64, ctx->b_t64,
-      ctx->D_r, ctx->out_m1, ctx->rec_a);
+      ctx->D_r, ctx->out_m1, ctx->rec_a, nullptr);
   k_brep_final<<<(count + 255) / 256, 256, 0, ctx->stream>>>(ctx->rec_t, ctx->lp_t8_tiles,
                                                              ctx->rec_a, ctx->lp_a8_tiles, count,
                                                              ctx->breport);

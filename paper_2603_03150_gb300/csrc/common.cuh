@@ -115,6 +115,15 @@ struct Scalars {
   int32_t log_count, log_cap;
   int32_t ticket;               // last-block-done counter for the eval kernel
   int32_t pad;
+  // float32-mixed: a Section 2 test that passes on the float32 caches is a
+  // screen; the candidate is then re-evaluated in float64 (products
+  // recomputed from the float64 scaled matrices) and only that decides
+  double screen;                // the screen passes at eps * screen (>= 1)
+  long long checks, rejects;    // float64 checks run / rejected in this solve
+  int32_t fp64_check;           // 1: confirm a passing screen in float64
+  int32_t verify;               // 1: a float64 check is pending
+  int32_t verify_avg;           // ... of the average (1) or the current iterate (0)
+  int32_t pad2;
 };
 
 struct PowerState {

@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(BLOCK) k_report_n(SchedView S, const int32_t* 
                                                    const double* val, const double* x_s,
                                                    const double* y_s, const double* c_t,
                                                    const double* D_c, double* x_out, double* z_out,
-                                                   double* partials) {
+                                                   double* partials, const Scalars* gate) {
+  if (gate && !gate->verify) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[4 * (BLOCK / 32)];
   double* split_q = partials + 4 * (size_t)gridDim.x;
@@ -309,7 +310,8 @@ __global__ void __launch_bounds__(BLOCK) k_report_m(SchedView S, const int32_t* 
                                                    const double* val, const double* x_s,
                                                    const double* y_s, const double* b_t,
                                                    const double* D_r, double* y_out,
-                                                   double* partials) {
+                                                   double* partials, const Scalars* gate) {
+  if (gate && !gate->verify) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[4 * (BLOCK / 32)];
   double* split_q = partials + 4 * (size_t)gridDim.x;
@@ -364,18 +366,65 @@ void launch_report_n(const SchedView& S, const int32_t* rp, const int32_t* col, 
                      double* x_out, double* z_out, double* partials, const Launch& L,
                      cudaStream_t s) {
   k_report_n<kBlock><<<L.grid, kBlock, L.smem, s>>>(S, rp, col, val, x_s, y_s, c_t, D_c, x_out,
-                                                    z_out, partials);
+                                                    z_out, partials, nullptr);
 }
 void launch_report_m(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
                      const double* x_s, const double* y_s, const double* b_t, const double* D_r,
                      double* y_out, double* partials, const Launch& L, cudaStream_t s) {
   k_report_m<kBlock><<<L.grid, kBlock, L.smem, s>>>(S, rp, col, val, x_s, y_s, b_t, D_r, y_out,
-                                                    partials);
+                                                    partials, nullptr);
 }
 void launch_report_final(const double* pn, int gn, const double* pm, int gm, double* out,
                          cudaStream_t s) {
   k_report_final<<<1, 32, 0, s>>>(pn, gn, pm, gm, out);
 }
+
+// ---------------------------------------------------------------------------
+// Float64 check of a float32-mixed candidate that passed the screen (every
+// kernel returns at once unless a check is pending): the candidate in
+// float64, the report sums of its products recomputed from the float64
+// scaled matrices, then the Section 2 test at eps in one thread.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fp64_prep(IterBuffers<T> B, double* xs, double* ys) {
+  const Scalars* sc = B.sc;
+  if (!sc->verify) return;
+  const bool avg = sc->verify_avg != 0;
+  const T* x = avg ? B.x_avg : B.x;
+  const T* y = avg ? B.y_avg : B.y;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < B.n; j += stride) xs[j] = (double)x[j];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.m; i += stride) ys[i] = (double)y[i];
+}
+
+__global__ void k_fp64_final(Scalars* sc, const double* pn, int gn, const double* pm, int gm,
+                             long long* log_k, int32_t* log_flags, double* log_kkt) {
+  if (threadIdx.x != 0 || !sc->verify) return;
+  double u2 = 0, s3 = 0, u1 = 0, s4 = 0;
+  for (int b = 0; b < gn; ++b) {
+    u2 += pn[4 * b];
+    s3 += pn[4 * b + 1];
+  }
+  for (int b = 0; b < gm; ++b) {
+    u1 += pm[4 * b];
+    s4 += pm[4 * b + 1];
+  }
+  eval_fp64_check(*sc, u1, u2, s3, s4, log_k, log_flags, log_kkt);
+}
+
+template <typename T>
+void launch_fp64_check(const IterBuffers<T>& B, const Fp64Check& C, cudaStream_t s) {
+  k_fp64_prep<T><<<C.conv_grid, 256, 0, s>>>(B, C.xs, C.ys);
+  double* pn = B.partials;
+  double* pm = B.partials + 4 * (size_t)(C.gn + 1);
+  k_report_n<kBlock><<<C.Lt.grid, kBlock, C.Lt.smem, s>>>(C.St, B.t_rp, B.t_col, C.t_val, C.xs, C.ys,
+                                                          B.c_t64, B.D_c, nullptr, nullptr, pn,
+                                                          B.sc);
+  k_report_m<kBlock><<<C.La.grid, kBlock, C.La.smem, s>>>(C.Sa, B.a_rp, B.a_col, C.a_val, C.xs, C.ys,
+                                                          B.b_t64, B.D_r, nullptr, pm, B.sc);
+  k_fp64_final<<<1, 32, 0, s>>>(B.sc, pn, C.gn, pm, C.gm, B.log_k, B.log_flags, B.log_kkt);
+}
+template void launch_fp64_check<float>(const IterBuffers<float>&, const Fp64Check&, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Algorithm 1 (Section 3.1), lines 2-11.

@@ -75,6 +75,21 @@ void launch_report_m(const SchedView& S, const int32_t* rp, const int32_t* col, 
 void launch_report_final(const double* pn, int gn, const double* pm, int gm, double* out,
                          cudaStream_t s);
 
+// Float64 check of a float32-mixed candidate whose screen passed (four
+// launches; each returns at once unless a check is pending): the float64
+// schedules and values of both matrices, conversion buffers and grids.
+struct Fp64Check {
+  SchedView St, Sa;            // float64 schedules of A~^T and A~
+  const double *t_val, *a_val;  // float64 scaled values
+  double *xs, *ys;             // candidate in float64 [n], [m]
+  Launch Lt, La;
+  int gn, gm;                  // block partials + split records of each report
+  int conv_grid;
+};
+template <typename T>
+void launch_fp64_check(const IterBuffers<T>& B, const Fp64Check& C, cudaStream_t s);
+constexpr int kFp64CheckLaunches = 4;
+
 // Algorithm 1 (Section 3.1)
 void launch_ws_z(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
                  const double* x_s, const double* y_s, const double* c_t, double* z_s,
@@ -160,6 +175,9 @@ cudaError_t configure_tile_kernels(size_t max_smem);
 void launch_panel_half(const IterBuffers<float>& B, const PanelView& V, bool dual, int method,
                        int row_grid, int i, cudaStream_t s, cudaEvent_t between = nullptr);
 size_t panel_smem(int P, int pscap);
+// the panel SpMV kernel of a half-step alone (timing)
+void launch_panel_spmv_only(const IterBuffers<float>& B, const PanelView& V, bool dual, int method,
+                            cudaStream_t s);
 // blocks of 256 threads for the row pass over `rows` rows of `npanels` panels
 int panel_row_grid(int rows, int npanels, int nsm);
 cudaError_t configure_panel_kernels(size_t max_smem);

@@ -1,13 +1,13 @@
-// Algorithm 1 centered start point on caller-provided device vectors with no
-// device allocation (pdhg_centered_point_noalloc in include/pdhg.h).
+// Algorithm 1 (Section 3.1) centered start point on caller-provided device
+// vectors with no device allocation (pdhg_centered_point_noalloc in
+// include/pdhg.h).
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is
-// being captured into a graph (allocation calls are not capturable), an
-// interior-point solver that owns a fixed device memory pool, or a host
-// thread that must not take the allocator's locks.  For them the scratch
-// this computation needs -- one partial sum of x^T z per block and
-// mu_target -- lives in a file-scope __device__ array that every GPU which
-// loads this library holds until the process exits.
+// Some callers cannot call cudaMalloc: an interior-point solver that owns a
+// fixed device memory pool and must not grow it, or a host thread that must
+// not take the device allocator's locks.  For them the scratch this
+// computation needs -- one partial sum of x^T z per block and mu_target --
+// lives in a file-scope __device__ array that every GPU which loads this
+// library holds until the process exits.
 #include <mutex>
 
 #include "common.cuh"
@@ -74,7 +74,9 @@ __global__ void k_na_apply(int n, const double* __restrict__ x, const double* __
   }
 }
 
-// Device address of g_na_scratch, looked up once per device.
+// Device address of g_na_scratch, looked up once per device (in the device's
+// primary context; a cudaDeviceReset would leave it stale, and the header
+// rules that out).
 std::mutex g_na_mutex;
 constexpr int kNaMaxDevices = 256;
 double* g_na_ptr[kNaMaxDevices] = {};

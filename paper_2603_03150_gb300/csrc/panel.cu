@@ -415,6 +415,13 @@ void launch_panel_half(const IterBuffers<float>& B, const PanelView& V, bool dua
   }
 }
 
+void launch_panel_spmv_only(const IterBuffers<float>& B, const PanelView& V, bool dual, int method,
+                            cudaStream_t s) {
+  const float* v = dual ? (method == 1 ? B.x_avg : B.x) : B.y;
+  launch_pdl(k_panel_spmv, V.nblocks, kPanelThreads, panel_smem(V.P, V.pscap), s, V, v,
+             (const Scalars*)B.sc);
+}
+
 int panel_row_grid(int rows, int npanels, int nsm) {
   const int64_t threads = (int64_t)rows * panel_lanes(npanels);
   return (int)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, (int64_t)nsm * 6));

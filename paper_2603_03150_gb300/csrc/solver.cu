@@ -304,13 +304,36 @@ static void launch_dual_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i,
 }
 static int prim_launches(const pdhg_ctx* ctx) { return ctx->pt.on ? 2 : 1; }
 static int dual_launches(const pdhg_ctx* ctx) { return ctx->pa.on ? 2 : 1; }
+// kernels of a chunk of `len` iterations: the half-steps, the evaluation, the
+// float64 check (float32-mixed) and the restart
+static long long chunk_launches(const pdhg_ctx* ctx, int len) {
+  return (long long)(prim_launches(ctx) + dual_launches(ctx)) * len + 2 +
+         (ctx->mixed ? kFp64CheckLaunches : 0);
+}
+
+// what the float64 check of a float32-mixed candidate reads and writes
+static Fp64Check fp64_check_args(pdhg_ctx* ctx) {
+  Fp64Check C{};
+  C.St = ctx->st8.view;
+  C.Sa = ctx->sa8.view;
+  C.t_val = ctx->t_val64;
+  C.a_val = ctx->a_val64;
+  C.xs = ctx->xs64;
+  C.ys = ctx->ys64;
+  C.Lt = ctx->l_t64;
+  C.La = ctx->l_a64;
+  C.gn = ctx->l_t64.grid + ctx->st8.view.ngroups;
+  C.gm = ctx->l_a64.grid + ctx->sa8.view.ngroups;
+  C.conv_grid = ctx->restart_grid;
+  return C;
+}
 
 // `len` iterations followed by the evaluation and the restart.  With
 // `timing`, events bracket the primal and dual kernels of iteration len/2.
 template <typename T>
 static void enqueue_chunk(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
   const IterBuffers<T> B = iter_buffers<T>(ctx);
-  ctx->launches += (long long)(prim_launches(ctx) + dual_launches(ctx)) * len + 2;
+  ctx->launches += chunk_launches(ctx, len);
   for (int i = 0; i < len; ++i) {
     const bool sample = timing && i == len / 2;
     if (sample) cudaEventRecordWithFlags(timing[0], ctx->stream, cudaEventRecordExternal);
@@ -323,6 +346,7 @@ static void enqueue_chunk(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
     if (sample) cudaEventRecordWithFlags(timing[5], ctx->stream, cudaEventRecordExternal);
   }
   launch_eval<T>(B, ctx->l_eval, len, ctx->stream);
+  if constexpr (sizeof(T) == 4) launch_fp64_check<T>(B, fp64_check_args(ctx), ctx->stream);
   launch_restart<T>(B, ctx->restart_grid, ctx->stream);
 }
 
@@ -566,6 +590,7 @@ extern "C" void pdhg_default_options(pdhg_options* o) {
   o->reflection = 1.0;
   o->spmv_layout = 0;
   o->panel_width = 0;
+  o->fp32_screen = 1.0;
 }
 
 // device attributes, stream, kernel shared-memory limits
@@ -917,10 +942,11 @@ extern "C" pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const i
       ctx->opt.tile_nnz < -8 || ctx->opt.tile_nnz > 8192 ||
       (ctx->opt.method != 0 && ctx->opt.method != 1) ||
       !(ctx->opt.reflection >= 0.0 && ctx->opt.reflection <= 1.0) ||
-      ctx->opt.spmv_layout < 0 || ctx->opt.spmv_layout > 2 || ctx->opt.panel_width < 0) {
+      ctx->opt.spmv_layout < 0 || ctx->opt.spmv_layout > 2 || ctx->opt.panel_width < 0 ||
+      !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6)) {
     set_error("invalid options (eval_freq >= 1, ruiz_iters >= 0, precision 0/1, "
               "-8 <= tile_nnz <= 8192, method 0/1, 0 <= reflection <= 1, spmv_layout 0..2, "
-              "panel_width >= 0)");
+              "panel_width >= 0, 1 <= fp32_screen <= 1e6)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }
@@ -990,6 +1016,11 @@ extern "C" pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_ite
   hs.status = PDHG_MAX_ITER;
   hs.restart_pending = 0;
   hs.ticket = 0;
+  hs.fp64_check = ctx->mixed ? 1 : 0;
+  hs.screen = ctx->opt.fp32_screen;
+  hs.verify = 0;
+  hs.checks = 0;
+  hs.rejects = 0;
   CK(cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
   if (ctx->opt.use_graphs) CKS(build_graphs(ctx));
   for (double& v : ctx->timing_sum) v = 0.0;
@@ -1024,7 +1055,7 @@ extern "C" pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_ite
     const int len = (int)(next - k);
     if (len == F && ctx->opt.use_graphs) {
       CK(cudaGraphLaunch(ctx->chunk_exec[slot], ctx->stream));
-      ctx->launches += 2 * F + 2;
+      ctx->launches += chunk_launches(ctx, (int)F);
       sampled[slot] = ctx->opt.kernel_timing != 0;
     } else {
       enqueue_chunk_any(ctx, len, nullptr);
@@ -1408,6 +1439,111 @@ extern "C" pdhg_status pdhg_get_kernel_timing_parts(pdhg_ctx* ctx, double* ms, i
   return PDHG_OK;
 }
 
+// Mean duration of back-to-back launches of each half-step on the context's
+// current state (the solver state is saved first and restored after).
+template <typename T>
+static pdhg_status time_kernels_impl(pdhg_ctx* ctx, int reps, double* ms) {
+  const IterBuffers<T> B = iter_buffers<T>(ctx);
+  const size_t es = sizeof(T), n = (size_t)ctx->n, m = (size_t)ctx->m;
+  // what a half-step writes: x, x_avg (n side); y, y_avg, Ax, Ax_avg (m side)
+  void* nvec[2] = {ctx->x, ctx->x_avg};
+  void* mvec[4] = {ctx->y, ctx->y_avg, ctx->Ax, ctx->Ax_avg};
+  char* save = nullptr;
+  const size_t bytes = es * (2 * n + 4 * m) + sizeof(Scalars);
+  CK(cudaMalloc(&save, bytes));
+  struct Free {
+    char* p;
+    ~Free() { cudaFree(p); }
+  } guard{save};
+  auto snapshot = [&](bool restore) -> pdhg_status {
+    size_t off = 0;
+    for (void* v : nvec) {
+      CK(restore ? cudaMemcpyAsync(v, save + off, es * n, cudaMemcpyDeviceToDevice, ctx->stream)
+                 : cudaMemcpyAsync(save + off, v, es * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      off += es * n;
+    }
+    for (void* v : mvec) {
+      CK(restore ? cudaMemcpyAsync(v, save + off, es * m, cudaMemcpyDeviceToDevice, ctx->stream)
+                 : cudaMemcpyAsync(save + off, v, es * m, cudaMemcpyDeviceToDevice, ctx->stream));
+      off += es * m;
+    }
+    CK(restore ? cudaMemcpyAsync(ctx->sc, save + off, sizeof(Scalars), cudaMemcpyDeviceToDevice,
+                                 ctx->stream)
+               : cudaMemcpyAsync(save + off, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    return PDHG_OK;
+  };
+  CKS(snapshot(false));
+  // the kernels do nothing once a solve has finished: run them as mid-solve
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  hs.done = 0;
+  hs.verify = 0;
+  CK(cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // which: 0 primal half-step, 1 dual, 2 iteration, 3 primal panel SpMV, 4 dual panel SpMV
+  auto run = [&](int which) {
+    switch (which) {
+      case 0: launch_prim_step<T>(ctx, B, 0); break;
+      case 1: launch_dual_step<T>(ctx, B, 0); break;
+      case 2:
+        launch_prim_step<T>(ctx, B, 0);
+        launch_dual_step<T>(ctx, B, 0);
+        break;
+      case 3:
+        if constexpr (sizeof(T) == 4) launch_panel_spmv_only(B, ctx->pt.view, false, ctx->opt.method, ctx->stream);
+        break;
+      default:
+        if constexpr (sizeof(T) == 4) launch_panel_spmv_only(B, ctx->pa.view, true, ctx->opt.method, ctx->stream);
+        break;
+    }
+  };
+  const int warm = 3;
+  pdhg_status st = PDHG_OK;
+  for (int which = 0; which < 5 && st == PDHG_OK; ++which) {
+    ms[which] = 0.0;
+    if ((which == 3 && !(ctx->mixed && ctx->pt.on)) || (which == 4 && !(ctx->mixed && ctx->pa.on)))
+      continue;
+    const long long per = which == 0 ? prim_launches(ctx) : which == 1 ? dual_launches(ctx)
+                          : which == 2 ? prim_launches(ctx) + dual_launches(ctx) : 1;
+    ctx->launches += per * (warm + reps);
+    for (int it = 0; it < warm + reps; ++it) {
+      if (it == warm) cudaEventRecord(e0, ctx->stream);
+      run(which);
+    }
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error("kernel timing: %s", cudaGetErrorString(e));
+      st = PDHG_CUDA_ERROR;
+      break;
+    }
+    ms[which] = (double)t / reps;
+    if (snapshot(true) != PDHG_OK) st = PDHG_CUDA_ERROR;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CKS(st);
+  CKS(snapshot(true));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_time_kernels(pdhg_ctx* ctx, int32_t reps, double* ms) {
+  g_last_error.clear();
+  if (!ctx || ctx->batch || reps < 1 || !ms) {
+    set_error("need a single-LP context, reps >= 1 and ms[5]");
+    return PDHG_INVALID_ARG;
+  }
+  return ctx->mixed ? time_kernels_impl<float>(ctx, reps, ms) : time_kernels_impl<double>(ctx, reps, ms);
+}
+
 extern "C" pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int32_t* a_block,
                                          int32_t* a_tiles, int32_t* at_tile_nnz,
                                          int32_t* at_block, int32_t* at_tiles,
@@ -1425,6 +1561,26 @@ extern "C" pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int
   if (at_tiles) *at_tiles = ctx->st.view.ntiles;
   if (a_variant) *a_variant = ctx->sa.view.e;
   if (at_variant) *at_variant = ctx->st.view.e;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_fp64_checks(pdhg_ctx* ctx, int64_t* checks, int64_t* rejects) {
+  g_last_error.clear();
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return PDHG_INVALID_ARG;
+  }
+  std::vector<Scalars> hs((size_t)ctx->count);
+  CK(cudaMemcpyAsync(hs.data(), ctx->sc, sizeof(Scalars) * hs.size(), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  long long c = 0, r = 0;
+  for (const Scalars& s : hs) {
+    c += s.checks;
+    r += s.rejects;
+  }
+  if (checks) *checks = c;
+  if (rejects) *rejects = r;
   return PDHG_OK;
 }
 

@@ -56,6 +56,7 @@ class Options(ctypes.Structure):
         ("reflection", ctypes.c_double),
         ("spmv_layout", ctypes.c_int32),
         ("panel_width", ctypes.c_int32),
+        ("fp32_screen", ctypes.c_double),
     ]
 
 
@@ -91,6 +92,8 @@ _SIGS = {
     "pdhg_set_caches": (_I32, [_P, _P, _P, _P]),
     "pdhg_get_kernel_timing_parts": (_I32, [_P, _P, _P]),
     "pdhg_get_launch_count": (_I32, [_P, _P]),
+    "pdhg_get_fp64_checks": (_I32, [_P, _P, _P]),
+    "pdhg_time_kernels": (_I32, [_P, _I32, _P]),
     "pdhg_gather_floor": (_I32, [_P, _I32, _I32, _P]),
     "pdhg_batch_create": (_I32, [_PP, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
     "pdhg_batch_solve": (_I32, [_P, _D, _I64, _P]),
@@ -175,7 +178,7 @@ class Solver:
                  use_graphs: bool = True, autotune: bool = True, tile_nnz: int = 0,
                  kernel_timing: bool = False, method: str = "averaged",
                  reflection: float = 1.0, spmv_layout: str = "auto", panel_width: int = 0,
-                 verbose: bool = False):
+                 fp32_screen: float = 1.0, verbose: bool = False):
         L = lib()
         o = Options()
         L.pdhg_default_options(ctypes.byref(o))
@@ -201,6 +204,7 @@ class Solver:
             raise ValueError("spmv_layout must be 'auto', 'csr' or 'panels'")
         o.spmv_layout = layouts[spmv_layout]
         o.panel_width = panel_width
+        o.fp32_screen = fp32_screen
         o.verbose = 1 if verbose else 0
         self.m, self.n = int(m), int(n)
         self.device_io = device_io
@@ -359,6 +363,22 @@ class Solver:
         ms = _D()
         _check(self._L.pdhg_gather_floor(self._ctx, 1 if on_a else 0, reps, ctypes.byref(ms)))
         return ms.value
+
+    def time_kernels(self, reps: int = 50):
+        """Mean ms of back-to-back launches of each half-step on the current
+        iterate (state saved and restored): primal, dual, iteration, and the
+        panel SpMV kernels alone (0 on CSR tiles)."""
+        ms = (ctypes.c_double * 5)()
+        _check(self._L.pdhg_time_kernels(self._ctx, reps, ms), allow_positive=False)
+        return dict(primal_ms=ms[0], dual_ms=ms[1], iteration_ms=ms[2], primal_spmv_ms=ms[3],
+                    dual_spmv_ms=ms[4])
+
+    def fp64_checks(self):
+        """Float64 checks of float32-mixed candidates in the last solve:
+        (run, rejected)."""
+        c, r = _I64(), _I64()
+        _check(self._L.pdhg_get_fp64_checks(self._ctx, ctypes.byref(c), ctypes.byref(r)))
+        return c.value, r.value
 
     def launch_count(self) -> int:
         v = _I64()

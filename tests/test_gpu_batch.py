@@ -67,11 +67,28 @@ def test_batch_fp32_mixed_all_converge():
     xs, ys = s.split(g["x"], "n"), s.split(g["y"], "m")
     for i, lp in enumerate(lps):
         A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
-        ok, rp, rd, gap = O.termination_test(A, lp.b, lp.c, xs[i], ys[i], 1e-4 * 1.01)
+        ok, rp, rd, gap = O.termination_test(A, lp.b, lp.c, xs[i], ys[i], 1e-4)
         assert ok, (i, rp, rd, gap)
         assert abs(rp - g["r_P"][i]) <= 1e-9 * (1 + rp)
         obj = float(lp.c @ lp.x_star)
         assert abs(float(lp.c @ xs[i]) - obj) <= 1e-3 * (1 + abs(obj))
+
+
+def test_batch_fp32_screen_rejections_per_lp():
+    """With a loose float32 screen (100 eps) every LP's early candidates are
+    re-evaluated in float64 and rejected; each LP still ends on a candidate
+    that meets the Section 2 test at eps."""
+    lps = lpgen.planted_batch(count=12, m_lo=50, m_hi=600)
+    with pdhg.BatchSolver(lps, precision="fp32", fp32_screen=100.0) as s:
+        assert s.solve(1e-4, 200_000) == pdhg.PDHG_CONVERGED
+        g = s.get()
+        checks, rejects = s.fp64_checks()
+    assert rejects >= 1 and checks == rejects + len(lps)
+    xs, ys = s.split(g["x"], "n"), s.split(g["y"], "m")
+    for i, lp in enumerate(lps):
+        A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+        ok, rp, rd, gap = O.termination_test(A, lp.b, lp.c, xs[i], ys[i], 1e-4)
+        assert ok, (i, rp, rd, gap)
 
 
 def test_batch_of_one_equals_single_lp_path():

@@ -1,0 +1,76 @@
+"""The bench's power-law LP at full size (m = 200,000, n = 1,000,000, exactly
+5,000,000 nonzeros, power-law row lengths up to 20,000, 1% of rows x 1e3),
+in the launch configuration the bench times (autotuned schedules), against
+the float64 oracle:
+
+  * float64: after 100 iterations (one restart-rule evaluation at k = 64,
+    the termination test at k = 100) the iterates, running averages and
+    primal weight equal the oracle's to 1e-9 relative (infinity norm) and the
+    restart log is the oracle's;
+  * float32-mixed: a solve to eps_rel = 1e-4 meets the Section 2 test at
+    1e-4 when the oracle re-evaluates the returned point in float64 (the
+    library confirms every screened candidate in float64 before it stops),
+    its objective is within 1e-3 relative of the planted optimum, and the
+    Section 4.3 maximum violation the library reports equals the oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import pdhg_oracle as O
+from paper_2603_03150_gb300 import build as B
+from paper_2603_03150_gb300 import lpgen, pdhg
+
+from test_gpu_parity import rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c1():
+    B.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return lpgen.powerlaw_lp(seed=0)
+
+
+@pytest.fixture(scope="module")
+def oracle_100(c1):
+    return O.solve(c1, 1e-12, 100)
+
+
+def test_fullsize_fp64_iterates_after_100_match_oracle(c1, oracle_100):
+    r = oracle_100
+    with pdhg.Solver.from_lp(c1) as s:
+        assert s.solve(1e-12, 100) == pdhg.PDHG_MAX_ITER
+        st = s.state()
+        lg = s.log()
+    for key, ref in (("x", r.state.x), ("y", r.state.y), ("x_avg", r.state.x_avg),
+                     ("y_avg", r.state.y_avg), ("x_last", r.state.x_last),
+                     ("y_last", r.state.y_last)):
+        assert rel_inf(st[key], ref) < 1e-9, key
+    assert st["k"] == r.state.k == 100 and st["t"] == r.state.t
+    assert st["restarts"] == r.state.restarts
+    assert abs(st["omega"] - r.state.omega) <= 1e-9 * r.state.omega
+    assert [(e["k"], e["restart"], e["cand"], e["r1"], e["r2"], e["r3"]) for e in lg] == \
+           [(e["k"], e["restart"], e["cand"], e["r1"], e["r2"], e["r3"]) for e in r.log]
+    for e, o in zip(lg, r.log):
+        assert abs(e["kkt_cur"] - o["kkt_cur"]) <= 1e-9 * o["kkt_cur"]
+        assert abs(e["kkt_avg"] - o["kkt_avg"]) <= 1e-9 * o["kkt_avg"]
+
+
+def test_fullsize_fp32_mixed_solve_meets_the_test_in_fp64(c1):
+    eps = 1e-4
+    with pdhg.Solver.from_lp(c1, precision="fp32") as s:
+        assert s.solve(eps, 2_000_000) == pdhg.PDHG_CONVERGED
+        g = s.get()
+        info = s.info()
+        checks, rejects = s.fp64_checks()
+    assert checks == rejects + 1
+    A = O.as_csr(c1.m, c1.n, c1.row_ptr, c1.col, c1.val)
+    ok, rp, rd, gap = O.termination_test(A, c1.b, c1.c, g["x"], g["y"], eps)
+    assert ok, (rp, rd, gap)
+    assert abs(g["r_P"] - rp) <= 1e-9 * (1 + rp) and abs(g["r_D"] - rd) <= 1e-9 * (1 + rd)
+    obj = float(c1.c @ c1.x_star)
+    assert abs(float(c1.c @ g["x"]) - obj) <= 1e-3 * (1 + abs(obj))
+    mv = O.max_violation(A, c1.b, c1.c, g["x"], g["y"])
+    assert abs(info["max_violation"] - mv) <= 1e-9 * (1 + mv)

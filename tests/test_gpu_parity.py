@@ -204,12 +204,46 @@ def test_fp32_mixed_converges_and_holds_in_fp64(maker):
     with pdhg.Solver.from_lp(lp, precision="fp32") as s:
         assert s.solve(1e-4, 200_000) == pdhg.PDHG_CONVERGED
         g = s.get()
+        checks, rejects = s.fp64_checks()
     eps = 1e-4
     A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
-    ok, rp, rd, gap = O.termination_test(A, lp.b, lp.c, g["x"], g["y"], eps * 1.01)
+    # the float64 check decides convergence: the Section 2 test holds at eps itself
+    ok, rp, rd, gap = O.termination_test(A, lp.b, lp.c, g["x"], g["y"], eps)
     assert ok, (rp, rd, gap)
+    assert checks - rejects == 1
     obj = float(lp.c @ r.x)
     assert abs(float(lp.c @ g["x"]) - obj) <= 1e-3 * (1 + abs(obj))
+
+
+@pytest.mark.parametrize("layout", ["csr", "panels"])
+def test_fp32_screen_rejections_continue_the_solve(layout):
+    """A loose float32 screen (100 eps) passes long before the iterate meets
+    the test: each screened candidate is re-evaluated in float64, the early
+    ones are rejected and the solve goes on, and the one accepted meets the
+    Section 2 test at eps when the oracle re-evaluates it."""
+    lp = lpgen.planted_lp(1000, 2500, seed=3)
+    eps = 1e-4
+    kw = dict(spmv_layout=layout, panel_width=512) if layout == "panels" else dict(spmv_layout="csr")
+    with pdhg.Solver.from_lp(lp, precision="fp32", fp32_screen=100.0, **kw) as s:
+        if layout == "panels" and s.layout()["a"]["panels"] == 0:
+            pytest.skip("column panels do not apply to this LP")
+        assert s.solve(eps, 200_000) == pdhg.PDHG_CONVERGED
+        g = s.get()
+        checks, rejects = s.fp64_checks()
+        log = s.log()
+    assert rejects >= 1 and checks == rejects + 1
+    A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+    ok, rp, rd, gap = O.termination_test(A, lp.b, lp.c, g["x"], g["y"], eps)
+    assert ok, (rp, rd, gap)
+    # a rejected evaluation still applies the restart rule (it is logged)
+    assert len(log) >= rejects
+
+
+def test_fp64_context_runs_no_fp64_checks():
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    with pdhg.Solver.from_lp(lp) as s:
+        assert s.solve(1e-4, 100_000) == pdhg.PDHG_CONVERGED
+        assert s.fp64_checks() == (0, 0)
 
 
 # ----------------------------------------------------------------- a9
