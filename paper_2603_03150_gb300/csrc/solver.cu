@@ -1525,7 +1525,11 @@ static pdhg_status time_kernels_impl(pdhg_ctx* ctx, int reps, double* ms) {
       break;
     }
     ms[which] = (double)t / reps;
-    if (snapshot(true) != PDHG_OK) st = PDHG_CUDA_ERROR;
+    // the next measurement starts from the same state, again as mid-solve
+    if (snapshot(true) != PDHG_OK ||
+        cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess)
+      st = PDHG_CUDA_ERROR;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -275,3 +275,43 @@ def test_panels_are_deterministic_and_resume_from_a_checkpoint():
     for k in ("x", "y", "x_avg", "y_avg", "Ax", "Ax_avg"):
         assert np.array_equal(got[k], runs[0][k]), k
     assert got["k"] == runs[0]["k"] == 320 and got["restarts"] == runs[0]["restarts"]
+
+
+@pytest.mark.parametrize("layout", ["csr", "panels"])
+def test_time_kernels_times_real_work_and_leaves_the_state(layout):
+    """pdhg_time_kernels runs each half-step back to back on the current
+    iterate (as mid-solve, also after a finished solve) and restores the
+    state: the state after the call is bit-identical, a continued solve
+    repeats an uninterrupted one, and every timed kernel did work (a
+    half-step is slower than its panel SpMV alone; an iteration costs at
+    least the slower half-step)."""
+    lp = heavy_row_lp(3)
+    kw = dict(precision="fp32", spmv_layout=layout, panel_width=2048)
+    with pdhg.Solver.from_lp(lp, **kw) as s:
+        s.solve(1e-12, 100)
+        before = s.state()
+        ms = s.time_kernels(20)
+        after = s.state()
+        for k in ("x", "y", "x_avg", "y_avg", "Ax", "Ax_avg"):
+            assert np.array_equal(before[k], after[k]), k
+        assert (before["k"], before["t"], before["omega"]) == (after["k"], after["t"], after["omega"])
+        s.solve(1e-12, 200)
+        cont = s.state()
+    with pdhg.Solver.from_lp(lp, **kw) as s2:
+        s2.solve(1e-12, 200)
+        ref = s2.state()
+    for k in ("x", "y", "x_avg", "y_avg"):
+        assert np.array_equal(cont[k], ref[k]), k
+    assert ms["primal_ms"] > 0 and ms["dual_ms"] > 0
+    assert ms["iteration_ms"] >= 0.8 * max(ms["primal_ms"], ms["dual_ms"])
+    if layout == "panels":
+        assert 0 < ms["primal_spmv_ms"] < ms["primal_ms"] and 0 < ms["dual_spmv_ms"] < ms["dual_ms"]
+    else:
+        assert ms["primal_spmv_ms"] == 0 and ms["dual_spmv_ms"] == 0
+    # after a finished solve the kernels are still timed as mid-solve
+    with pdhg.Solver.from_lp(lpgen.planted_lp(200, 500, seed=0), **kw) as s3:
+        assert s3.solve(1e-4, 100_000) == pdhg.PDHG_CONVERGED
+        ms3 = s3.time_kernels(20)
+        ms3b = s3.time_kernels(20)
+        assert s3.info(violation=False)["status"] == pdhg.PDHG_CONVERGED
+    assert ms3["dual_ms"] > 0 and ms3b["dual_ms"] > 0
