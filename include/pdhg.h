@@ -112,6 +112,19 @@ typedef struct pdhg_options {
                               that test at eps_rel ends the solve (a rejected
                               candidate continues: the restart rule of that
                               evaluation is applied as usual)                  */
+  int32_t omega_rule;      /* primal weight at a restart, with dx, dy the primal
+                              and dual distances moved since the last restart
+                              point (both > 1e-10, else omega is kept):
+                              0 (default): exp(theta log(dy/dx) + (1 - theta)
+                              log omega);
+                              1: PID control of log omega, the reading of
+                              cuPDLP+'s primal-weight control (Section 4.1
+                              names cuPDLP+): e = log(dy/dx) - log omega,
+                              I += e, log omega += pid_kp e + pid_ki I +
+                              pid_kd (e - e_prev)                              */
+  double pid_kp;           /* proportional gain (default 0.99)                  */
+  double pid_ki;           /* integral gain (default 0.01)                      */
+  double pid_kd;           /* derivative gain (default 0)                       */
 } pdhg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -148,6 +161,12 @@ pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_iter);
  * ||r_P||_2, ||r_D||_2, |c^T x - b^T y|, all evaluated in float64.  */
 pdhg_status pdhg_get(pdhg_ctx* ctx, double* x, double* y, double* z, double* r_P,
                      double* r_D, double* gap);
+
+/* The PID primal-weight controller's state (options.omega_rule = 1): the
+ * sum of its errors so far and its last error; part of a checkpoint beside
+ * pdhg_get_state / pdhg_set_state.  Single-LP contexts.  */
+pdhg_status pdhg_get_pid_state(pdhg_ctx* ctx, double* integral, double* prev_error);
+pdhg_status pdhg_set_pid_state(pdhg_ctx* ctx, double integral, double prev_error);
 
 /* Float64 checks of float32-mixed candidates in the last solve (single LP
  * or summed over a batch): how many screened candidates were re-evaluated

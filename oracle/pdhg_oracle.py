@@ -44,6 +44,9 @@ CUDA path implements independently:
   primal-weight update with theta = 0.5.
 These constants are a convention shared with the CUDA path: parity unpinned
 against the paper for the restart constants, the omega rule and eta.
+Optional primal-weight rule (``Options.omega_rule = "pid"``): PID control of
+log omega at each restart, the reading of cuPDLP+'s primal-weight control
+(``omega_update_pid``; gains kp = 0.99, ki = 0.01, kd = 0 by default).
 
 Optional iteration (``Options.method = "halpern"``): the reflected Halpern
 scheme of cuPDLP+, the solver Section 4.1 says its PDHG follows (the paper
@@ -87,6 +90,10 @@ class Options:
     omega_update_min: float = 1e-10
     method: str = "averaged"   # or "halpern" (reflected Halpern, see the header)
     reflection: float = 1.0    # rho of the Halpern method, in [0, 1]
+    omega_rule: str = "smooth"  # or "pid" (PID control of log omega, see omega_update_pid)
+    pid_kp: float = 0.99
+    pid_ki: float = 0.01
+    pid_kd: float = 0.0
 
 
 # ---------------------------------------------------------------------------
@@ -286,6 +293,27 @@ def omega_update(dx: float, dy: float, omega: float, theta: float = 0.5,
     return float(omega)
 
 
+def omega_update_pid(dx: float, dy: float, omega: float, integral: float, prev_error: float,
+                     kp: float = 0.99, ki: float = 0.01, kd: float = 0.0,
+                     min_dist: float = 1e-10):
+    """Primal weight at a restart under PID control of log omega (the
+    reading of cuPDLP+'s primal-weight control, the solver Section 4.1 says
+    the paper's PDHG follows).  The error is the log of the ratio of the
+    dual to the primal distance moved since the last restart point, against
+    the current weight:
+        e = log(dy / dx) - log(omega),   I <- I + e,
+        log omega <- log omega + kp e + ki I + kd (e - e_prev).
+    With ki = kd = 0 this is the smoothing of omega_update with theta = kp.
+    Unchanged (weight, integral and previous error) unless both distances
+    exceed min_dist.  Returns (omega, integral, error)."""
+    if dx > min_dist and dy > min_dist:
+        e = float(np.log(dy / dx) - np.log(omega))
+        integral = integral + e
+        lw = float(np.log(omega)) + kp * e + ki * integral + kd * (e - prev_error)
+        return float(np.exp(lw)), float(integral), e
+    return float(omega), float(integral), float(prev_error)
+
+
 # ---------------------------------------------------------------------------
 # the restarted loop (a4-a8)
 # ---------------------------------------------------------------------------
@@ -332,6 +360,8 @@ class State:
     restarts: int = 0
     kkt_last: float = 0.0   # KKT error of the last restart point
     kkt_prev: float = 0.0   # KKT error of the previous evaluation's candidate
+    pid_integral: float = 0.0  # omega_rule "pid": sum of the errors so far
+    pid_prev: float = 0.0      # omega_rule "pid": the previous restart's error
 
 
 @dataclass
@@ -396,6 +426,8 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
     halpern = opts.method == "halpern"
     if opts.method not in ("averaged", "halpern") or not 0.0 <= opts.reflection <= 1.0:
         raise ValueError("method must be 'averaged' or 'halpern', reflection in [0, 1]")
+    if opts.omega_rule not in ("smooth", "pid"):
+        raise ValueError("omega_rule must be 'smooth' or 'pid'")
     while st.k < max_iter:
         tau, sigma = S.eta / st.omega, S.eta * st.omega
         if halpern:
@@ -441,14 +473,19 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
             yc = st.y_avg if use_avg else st.y
             dx = float(np.linalg.norm(xc - st.x_last))
             dy = float(np.linalg.norm(yc - st.y_last))
-            st.omega = omega_update(dx, dy, st.omega, opts.theta, opts.omega_update_min)
+            if opts.omega_rule == "pid":
+                st.omega, st.pid_integral, st.pid_prev = omega_update_pid(
+                    dx, dy, st.omega, st.pid_integral, st.pid_prev, opts.pid_kp, opts.pid_ki,
+                    opts.pid_kd, opts.omega_update_min)
+            else:
+                st.omega = omega_update(dx, dy, st.omega, opts.theta, opts.omega_update_min)
             st.x, st.y = xc.copy(), yc.copy()
             st.x_last, st.y_last = xc.copy(), yc.copy()
             st.x_avg = np.zeros_like(st.x)
             st.y_avg = np.zeros_like(st.y)
             st.t = 0
             st.restarts += 1
-            entry.update(dx=dx, dy=dy, omega_new=st.omega)
+            entry.update(dx=dx, dy=dy, omega_new=st.omega, pid_integral=st.pid_integral)
         log.append(entry)
         xs_out, ys_out = st.x, st.y
 

@@ -1068,6 +1068,10 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
     h.beta_nec = ctx->opt.beta_necessary;
     h.beta_art = ctx->opt.beta_artificial;
     h.theta = ctx->opt.theta;
+    h.omega_rule = ctx->opt.omega_rule;
+    h.pid_kp = ctx->opt.pid_kp;
+    h.pid_ki = ctx->opt.pid_ki;
+    h.pid_kd = ctx->opt.pid_kd;
     h.log_cap = 0;
     h.status = PDHG_MAX_ITER;
     std::vector<Scalars> hv(count, h);
@@ -1148,7 +1152,8 @@ extern "C" pdhg_status pdhg_batch_create(pdhg_ctx** out, int32_t count, const in
     pdhg_default_options(&ctx->opt);
   if (ctx->opt.eval_freq < 1 ||
       (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED) ||
-      ctx->opt.method != 0 || !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6)) {
+      ctx->opt.method != 0 || !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6) ||
+      (ctx->opt.omega_rule != 0 && ctx->opt.omega_rule != 1)) {
     set_error("invalid options (eval_freq >= 1, precision 0/1, 1 <= fp32_screen <= 1e6, "
               "method 0: batched solves use the averaged iteration)");
     delete ctx;

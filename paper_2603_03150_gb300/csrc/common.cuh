@@ -123,7 +123,9 @@ struct Scalars {
   int32_t fp64_check;           // 1: confirm a passing screen in float64
   int32_t verify;               // 1: a float64 check is pending
   int32_t verify_avg;           // ... of the average (1) or the current iterate (0)
-  int32_t pad2;
+  int32_t omega_rule;           // 0: smoothing with theta; 1: PID control of log omega
+  double pid_kp, pid_ki, pid_kd;
+  double pid_integral, pid_prev;  // sum of the PID errors so far, the last error
 };
 
 struct PowerState {

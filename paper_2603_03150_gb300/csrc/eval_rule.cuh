@@ -90,8 +90,18 @@ __device__ inline void eval_restart(Scalars& sc, const double* tot, long long* l
   if (restart) {
     const double dx = sqrt(tot[cand * Q_N + Q_D1]);
     const double dy = sqrt(tot[cand * Q_N + Q_D2]);
-    if (dx > 1e-10 && dy > 1e-10)
-      sc.omega = exp(sc.theta * log(dy / dx) + (1.0 - sc.theta) * log(sc.omega));
+    if (dx > 1e-10 && dy > 1e-10) {
+      if (sc.omega_rule == 1) {
+        // PID control of log omega: e = log(dy/dx) - log omega, I += e
+        const double e = log(dy / dx) - log(sc.omega);
+        sc.pid_integral += e;
+        sc.omega = exp(log(sc.omega) + sc.pid_kp * e + sc.pid_ki * sc.pid_integral +
+                       sc.pid_kd * (e - sc.pid_prev));
+        sc.pid_prev = e;
+      } else {
+        sc.omega = exp(sc.theta * log(dy / dx) + (1.0 - sc.theta) * log(sc.omega));
+      }
+    }
     sc.tau = sc.eta / sc.omega;
     sc.sigma = sc.eta * sc.omega;
     sc.t = 0;

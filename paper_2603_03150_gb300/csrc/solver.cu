@@ -591,6 +591,10 @@ extern "C" void pdhg_default_options(pdhg_options* o) {
   o->spmv_layout = 0;
   o->panel_width = 0;
   o->fp32_screen = 1.0;
+  o->omega_rule = 0;
+  o->pid_kp = 0.99;
+  o->pid_ki = 0.01;
+  o->pid_kd = 0.0;
 }
 
 // device attributes, stream, kernel shared-memory limits
@@ -874,6 +878,10 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     h.beta_nec = ctx->opt.beta_necessary;
     h.beta_art = ctx->opt.beta_artificial;
     h.theta = ctx->opt.theta;
+    h.omega_rule = ctx->opt.omega_rule;
+    h.pid_kp = ctx->opt.pid_kp;
+    h.pid_ki = ctx->opt.pid_ki;
+    h.pid_kd = ctx->opt.pid_kd;
     h.log_cap = ctx->log_cap;
     h.status = PDHG_MAX_ITER;
     CK(cudaMemcpyAsync(ctx->sc, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
@@ -943,10 +951,13 @@ extern "C" pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const i
       (ctx->opt.method != 0 && ctx->opt.method != 1) ||
       !(ctx->opt.reflection >= 0.0 && ctx->opt.reflection <= 1.0) ||
       ctx->opt.spmv_layout < 0 || ctx->opt.spmv_layout > 2 || ctx->opt.panel_width < 0 ||
-      !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6)) {
+      !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6) ||
+      (ctx->opt.omega_rule != 0 && ctx->opt.omega_rule != 1) ||
+      !std::isfinite(ctx->opt.pid_kp) || !std::isfinite(ctx->opt.pid_ki) ||
+      !std::isfinite(ctx->opt.pid_kd)) {
     set_error("invalid options (eval_freq >= 1, ruiz_iters >= 0, precision 0/1, "
               "-8 <= tile_nnz <= 8192, method 0/1, 0 <= reflection <= 1, spmv_layout 0..2, "
-              "panel_width >= 0, 1 <= fp32_screen <= 1e6)");
+              "panel_width >= 0, 1 <= fp32_screen <= 1e6, omega_rule 0/1, finite PID gains)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }
@@ -1565,6 +1576,36 @@ extern "C" pdhg_status pdhg_get_schedule(pdhg_ctx* ctx, int32_t* a_tile_nnz, int
   if (at_tiles) *at_tiles = ctx->st.view.ntiles;
   if (a_variant) *a_variant = ctx->sa.view.e;
   if (at_variant) *at_variant = ctx->st.view.e;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_pid_state(pdhg_ctx* ctx, double* integral, double* prev_error) {
+  g_last_error.clear();
+  if (!ctx || ctx->batch) {
+    set_error("need a single-LP context");
+    return PDHG_INVALID_ARG;
+  }
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (integral) *integral = hs.pid_integral;
+  if (prev_error) *prev_error = hs.pid_prev;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_set_pid_state(pdhg_ctx* ctx, double integral, double prev_error) {
+  g_last_error.clear();
+  if (!ctx || ctx->batch || !std::isfinite(integral) || !std::isfinite(prev_error)) {
+    set_error("need a single-LP context and finite values");
+    return PDHG_INVALID_ARG;
+  }
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  hs.pid_integral = integral;
+  hs.pid_prev = prev_error;
+  CK(cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return PDHG_OK;
 }
 

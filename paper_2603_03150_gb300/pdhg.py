@@ -57,6 +57,10 @@ class Options(ctypes.Structure):
         ("spmv_layout", ctypes.c_int32),
         ("panel_width", ctypes.c_int32),
         ("fp32_screen", ctypes.c_double),
+        ("omega_rule", ctypes.c_int32),
+        ("pid_kp", ctypes.c_double),
+        ("pid_ki", ctypes.c_double),
+        ("pid_kd", ctypes.c_double),
     ]
 
 
@@ -94,6 +98,8 @@ _SIGS = {
     "pdhg_get_launch_count": (_I32, [_P, _P]),
     "pdhg_get_fp64_checks": (_I32, [_P, _P, _P]),
     "pdhg_time_kernels": (_I32, [_P, _I32, _P]),
+    "pdhg_get_pid_state": (_I32, [_P, _P, _P]),
+    "pdhg_set_pid_state": (_I32, [_P, _D, _D]),
     "pdhg_gather_floor": (_I32, [_P, _I32, _I32, _P]),
     "pdhg_batch_create": (_I32, [_PP, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
     "pdhg_batch_solve": (_I32, [_P, _D, _I64, _P]),
@@ -178,7 +184,8 @@ class Solver:
                  use_graphs: bool = True, autotune: bool = True, tile_nnz: int = 0,
                  kernel_timing: bool = False, method: str = "averaged",
                  reflection: float = 1.0, spmv_layout: str = "auto", panel_width: int = 0,
-                 fp32_screen: float = 1.0, verbose: bool = False):
+                 fp32_screen: float = 1.0, omega_rule: str = "smooth", pid_kp: float = 0.99,
+                 pid_ki: float = 0.01, pid_kd: float = 0.0, verbose: bool = False):
         L = lib()
         o = Options()
         L.pdhg_default_options(ctypes.byref(o))
@@ -205,6 +212,10 @@ class Solver:
         o.spmv_layout = layouts[spmv_layout]
         o.panel_width = panel_width
         o.fp32_screen = fp32_screen
+        if omega_rule not in ("smooth", "pid"):
+            raise ValueError("omega_rule must be 'smooth' or 'pid'")
+        o.omega_rule = 1 if omega_rule == "pid" else 0
+        o.pid_kp, o.pid_ki, o.pid_kd = pid_kp, pid_ki, pid_kd
         o.verbose = 1 if verbose else 0
         self.m, self.n = int(m), int(n)
         self.device_io = device_io
@@ -296,6 +307,9 @@ class Solver:
         d.update(zip(["Ax", "Ax_avg", "Ax_last"], caches))
         d.update(omega=sc[0], k=int(sc[1]), t=int(sc[2]), restarts=int(sc[3]),
                  kkt_last=sc[4], kkt_prev=sc[5], eta=sc[6])
+        pi, pe = _D(), _D()
+        _check(self._L.pdhg_get_pid_state(self._ctx, ctypes.byref(pi), ctypes.byref(pe)))
+        d.update(pid_integral=pi.value, pid_prev=pe.value)
         return d
 
     def set_state(self, st):
@@ -306,6 +320,10 @@ class Solver:
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
         _check(self._L.pdhg_set_state(self._ctx, *[_ptr(a) for a in arrs], _ptr(sc)),
                allow_positive=False)
+        if "pid_integral" in st:
+            _check(self._L.pdhg_set_pid_state(self._ctx, float(st["pid_integral"]),
+                                              float(st.get("pid_prev", 0.0))),
+                   allow_positive=False)
         if all(k in st for k in ("Ax", "Ax_avg", "Ax_last")):
             caches = [st[k] for k in ("Ax", "Ax_avg", "Ax_last")]
             if not self.device_io:

@@ -517,3 +517,67 @@ def test_bookkeeping_trace_catches_planted_slips(kind):
             last, prev = (d["k_cand"] if d["restart"] else last), e["kkt_cur"]
         wrong |= (last, prev) != (e["kkt_last"], e["kkt_prev"])
     assert wrong
+
+
+# --------------------------------------------------------------- PID primal weight
+def _pid_failures(update):
+    """Names of the hand-worked PID traces that `update`
+    (omega_update_pid's signature) gets wrong."""
+    bad = []
+    for tr in _load("pid_weight_cases.json")["traces"]:
+        w, I, e = tr["omega0"], tr["integral0"], tr["prev0"]
+        for st in tr["steps"]:
+            w, I, e = update(st["dx"], st["dy"], w, I, e, tr["kp"], tr["ki"], tr["kd"], 1e-10)
+            if (abs(w - st["omega"]) > 1e-14 * st["omega"] or abs(I - st["integral"]) > 1e-14
+                    or abs(e - st["error"]) > 1e-14):
+                bad.append(tr["name"])
+                break
+    return bad
+
+
+def test_pid_weight_hand_traces():
+    assert _pid_failures(O.omega_update_pid) == []
+
+
+def test_pid_with_kp_only_is_the_smoothing_rule():
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        dx, dy, w, th = rng.uniform(0.1, 10), rng.uniform(0.1, 10), rng.uniform(0.1, 10), rng.uniform(0, 1)
+        a = O.omega_update_pid(dx, dy, w, 0.0, 0.0, th, 0.0, 0.0)[0]
+        assert abs(a - O.omega_update(dx, dy, w, th)) <= 1e-13 * a
+
+
+def test_pid_default_gains_converge_to_a_constant_ratio():
+    """With the distances' ratio fixed at rho, the loop's fixed point is
+    omega = rho with no accumulated error (the integral returns to 0); with
+    the default gains the integral decays by about ki = 1% per restart."""
+    for rho, w in ((5.0, 1.0), (0.01, 30.0)):
+        I = e = 0.0
+        for _ in range(4000):
+            w, I, e = O.omega_update_pid(1.0, rho, w, I, e)
+        assert abs(np.log(w / rho)) < 1e-10 and abs(I) < 1e-8
+
+
+@pytest.mark.parametrize("kind", ["error_sign", "integral_before_update", "derivative_reversed",
+                                  "derivative_on_error"])
+def test_pid_traces_catch_planted_slips(kind):
+    def update(dx, dy, w, I, ep, kp, ki, kd, mn):
+        if not (dx > mn and dy > mn):
+            return w, I, ep
+        e = np.log(dy / dx) - np.log(w)
+        if kind == "error_sign":
+            e = -e
+        I_new = I + e
+        Iu = I if kind == "integral_before_update" else I_new
+        d = (ep - e) if kind == "derivative_reversed" else (e if kind == "derivative_on_error" else e - ep)
+        return float(np.exp(np.log(w) + kp * e + ki * Iu + kd * d)), float(I_new), float(e)
+    assert _pid_failures(update) != []
+
+
+def test_pid_solve_reaches_the_planted_optimum():
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    r = O.solve(lp, 1e-6, 200_000, opts=O.Options(omega_rule="pid"))
+    assert r.status == O.STATUS_CONVERGED
+    obj = float(lp.c @ lp.x_star)
+    assert abs(float(lp.c @ r.x) - obj) <= 1e-5 * (1 + abs(obj))
+    assert any("pid_integral" in e for e in r.log)
