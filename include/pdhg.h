@@ -296,6 +296,17 @@ pdhg_status pdhg_batch_create(pdhg_ctx** out, int32_t count, const int32_t* m, c
                               const int32_t* row_ptr, const int32_t* col, const double* val,
                               const double* b, const double* c, const pdhg_options* opt);
 
+/* New right-hand sides for every LP of a batch with the same A: b[sum m],
+ * c[sum n] (host or device as the context's other arrays), finite.  A's
+ * scaling, its transpose, the power iteration and the tuned schedules are
+ * kept (they depend on A only); b~ = D_r b, c~ = D_c c, the norms, the
+ * initial primal weight and step sizes are recomputed, and every LP starts
+ * again from x = 0, y = 0 with a fresh restart state, as a new context on
+ * (A, b, c) with the same tile schedules would.  The active set of a previous
+ * pdhg_batch_polish is dropped (polish again before pdhg_batch_adjoint).
+ * Non-finite data -> PDHG_INVALID_ARG (the context stays usable).  */
+pdhg_status pdhg_batch_set_rhs(pdhg_ctx* ctx, const double* b, const double* c);
+
 /* Iterate every LP (in lockstep, F iterations per chunk) until each has
  * passed the Section 2 test with eps_rel or the iteration count reaches
  * max_iter.  lp_status (HOST int32[count] or NULL) receives each LP's

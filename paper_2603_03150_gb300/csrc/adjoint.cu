@@ -308,6 +308,10 @@ struct AdjointData {
 
 static AdjointData* adj_of(pdhg_ctx* ctx) { return static_cast<AdjointData*>(ctx->adjoint); }
 
+void pdhg_adjoint_invalidate(pdhg_ctx* ctx) {
+  if (ctx->adjoint) adj_of(ctx)->polished = false;
+}
+
 void pdhg_free_adjoint(pdhg_ctx* ctx) {
   delete adj_of(ctx);
   ctx->adjoint = nullptr;

@@ -952,6 +952,34 @@ static pdhg_status tune_batch_schedules(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
+// every LP's scalar state as before its first iteration (the step sizes and
+// weights are set by k_binit from the power iteration and the scaled b, c)
+static pdhg_status batch_fresh_scalars(pdhg_ctx* ctx) {
+  Scalars h{};
+  h.eval_freq = ctx->opt.eval_freq;
+  h.beta_suff = ctx->opt.beta_sufficient;
+  h.beta_nec = ctx->opt.beta_necessary;
+  h.beta_art = ctx->opt.beta_artificial;
+  h.theta = ctx->opt.theta;
+  h.omega_rule = ctx->opt.omega_rule;
+  h.pid_kp = ctx->opt.pid_kp;
+  h.pid_ki = ctx->opt.pid_ki;
+  h.pid_kd = ctx->opt.pid_kd;
+  h.log_cap = 0;
+  h.status = PDHG_MAX_ITER;
+  std::vector<Scalars> hv(ctx->count, h);
+  CK(cudaMemcpyAsync(ctx->sc, hv.data(), sizeof(Scalars) * ctx->count, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+__global__ void k_bfinite(int64_t len, const double* __restrict__ v, int32_t* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[i])) atomicOr(flag, 1);
+}
+
 static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int32_t* n,
                                      const int32_t* row_ptr, const int32_t* col,
                                      const double* val, const double* b, const double* c) {
@@ -1014,6 +1042,8 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
   CKS(dalloc(ctx, &d_nnz_off, count + 1));
   CKS(dalloc(ctx, &d_m_off, count + 1));
   CKS(dalloc(ctx, &d_n_off, count + 1));
+  ctx->d_m_off = d_m_off;
+  ctx->d_n_off = d_n_off;
   CKS(dalloc(ctx, &flags, 1));
   CK(cudaMemcpyAsync(d_nnz_off, nnz_off.data(), sizeof(int64_t) * (count + 1),
                      cudaMemcpyHostToDevice, ctx->stream));
@@ -1056,29 +1086,12 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
   ctx->rec_tiles = std::max({A.ntiles, T.ntiles, A8.ntiles, T8.ntiles, 1});
   CKS(dalloc(ctx, &ctx->rec_t, (size_t)ctx->rec_tiles * kEvalQ));
   CKS(dalloc(ctx, &ctx->rec_a, (size_t)ctx->rec_tiles * kEvalQ));
-  CKS(dalloc(ctx, &ctx->active, 4));
+  CKS(dalloc(ctx, &ctx->active, 5));  // [4]: pdhg_batch_set_rhs's finiteness flag
   CKS(dalloc(ctx, &ctx->breport, (size_t)count * 8));
   CK(cudaMemsetAsync(ctx->active, 0, 4 * sizeof(int32_t), ctx->stream));
 
   // per-LP scalar state
-  {
-    Scalars h{};
-    h.eval_freq = ctx->opt.eval_freq;
-    h.beta_suff = ctx->opt.beta_sufficient;
-    h.beta_nec = ctx->opt.beta_necessary;
-    h.beta_art = ctx->opt.beta_artificial;
-    h.theta = ctx->opt.theta;
-    h.omega_rule = ctx->opt.omega_rule;
-    h.pid_kp = ctx->opt.pid_kp;
-    h.pid_ki = ctx->opt.pid_ki;
-    h.pid_kd = ctx->opt.pid_kd;
-    h.log_cap = 0;
-    h.status = PDHG_MAX_ITER;
-    std::vector<Scalars> hv(count, h);
-    CK(cudaMemcpyAsync(ctx->sc, hv.data(), sizeof(Scalars) * count, cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-  }
+  CKS(batch_fresh_scalars(ctx));
   // a3 per LP: power iteration
   {
     double *v = ctx->xs64, *u = ctx->ys64, *w = ctx->out_n2;
@@ -1190,6 +1203,48 @@ static pdhg_status build_batch_graphs(pdhg_ctx* ctx) {
     CK(cudaGraphInstantiate(&ctx->chunk_exec[g], graph, 0));
     cudaGraphDestroy(graph);
   }
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_batch_set_rhs(pdhg_ctx* ctx, const double* b, const double* c) {
+  clear_error();
+  if (!ctx || !ctx->batch || !b || !c) {
+    set_error("pdhg_batch_set_rhs needs a context from pdhg_batch_create and non-NULL b, c");
+    return PDHG_INVALID_ARG;
+  }
+  const int m = ctx->m, n = ctx->n;
+  CKS(copy_in(ctx, ctx->b, b, sizeof(double) * m));
+  CKS(copy_in(ctx, ctx->c, c, sizeof(double) * n));
+  int32_t* flag = ctx->active + 4;
+  CK(cudaMemsetAsync(flag, 0, sizeof(int32_t), ctx->stream));
+  k_bfinite<<<std::max(1, std::min(ctx->nsm * 4, (m + 255) / 256)), 256, 0, ctx->stream>>>(m, ctx->b, flag);
+  k_bfinite<<<std::max(1, std::min(ctx->nsm * 4, (n + 255) / 256)), 256, 0, ctx->stream>>>(n, ctx->c, flag);
+  int32_t hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->launches += 2;
+  if (hflag) {
+    set_error("b and c must be finite");
+    return PDHG_INVALID_ARG;
+  }
+  // scaled right-hand sides (the scaling depends on A only)
+  launch_scale_vec(m, ctx->D_r, ctx->b, ctx->b_t64, ctx->b_t32, ctx->stream);
+  launch_scale_vec(n, ctx->D_c, ctx->c, ctx->c_t64, ctx->c_t32, ctx->stream);
+  // every LP back to x = 0, y = 0 with fresh restart state
+  const size_t es = elem(ctx);
+  for (void* v : {ctx->x, ctx->x_avg, ctx->x_last}) CK(cudaMemsetAsync(v, 0, es * n, ctx->stream));
+  for (void* v : {ctx->y, ctx->y_avg, ctx->y_last, ctx->Ax, ctx->Ax_avg, ctx->Ax_last})
+    CK(cudaMemsetAsync(v, 0, es * m, ctx->stream));
+  CKS(batch_fresh_scalars(ctx));
+  k_binit<kBlock><<<ctx->count, kBlock, 0, ctx->stream>>>(ctx->sc, ctx->ps, ctx->d_m_off,
+                                                          ctx->d_n_off, ctx->b, ctx->c, ctx->b_t64,
+                                                          ctx->c_t64, ctx->opt.eta_safety);
+  ctx->launches += 3;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  pdhg_adjoint_invalidate(ctx);
+  ctx->report_valid = false;
+  ctx->last_status = PDHG_MAX_ITER;
   return PDHG_OK;
 }
 

@@ -80,6 +80,8 @@ struct DevPanel {
 
 struct pdhg_ctx;
 void pdhg_free_adjoint(pdhg_ctx* ctx);
+// the active set fixed by pdhg_batch_polish no longer applies (new b, c)
+void pdhg_adjoint_invalidate(pdhg_ctx* ctx);
 
 using pdhg::DevPanel;
 using pdhg::DevSched;
@@ -129,6 +131,7 @@ struct pdhg_ctx {
   double *rec_t = nullptr, *rec_a = nullptr;  // per-tile evaluation / report records
   int rec_tiles = 0;                          // tiles the record arrays hold
   int32_t* active = nullptr;                  // LPs not finished after the last evaluation
+  int64_t *d_m_off = nullptr, *d_n_off = nullptr;  // [count + 1] row / column offsets (device)
   double* breport = nullptr;                  // [count][8] per-LP report
   void* adjoint = nullptr;                    // active-set polish / adjoint buffers
   // schedules and launch shapes

@@ -103,6 +103,7 @@ _SIGS = {
     "pdhg_gather_floor": (_I32, [_P, _I32, _I32, _P]),
     "pdhg_batch_create": (_I32, [_PP, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
     "pdhg_batch_solve": (_I32, [_P, _D, _I64, _P]),
+    "pdhg_batch_set_rhs": (_I32, [_P, _P, _P]),
     "pdhg_batch_get": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pdhg_batch_warmstart_point": (_I32, [_P, _D, _D, _D, _I32, _P, _P, _P, _P]),
     "pdhg_batch_polish": (_I32, [_P, _D, _I32, _P, _P, _P]),
@@ -471,6 +472,16 @@ class BatchSolver(Solver):
         self.status = None
         self.m_off = np.concatenate([[0], np.cumsum(self.ms)]).astype(np.int64)
         self.n_off = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
+
+    def set_rhs(self, b, c):
+        """New b (float64 [sum m]) and c ([sum n]) for the same A: the scaling,
+        transpose, power iteration and schedules are kept; every LP restarts
+        from zero."""
+        if not self.device_io:
+            b = b if _is_torch(b) else np.ascontiguousarray(b, dtype=np.float64)
+            c = c if _is_torch(c) else np.ascontiguousarray(c, dtype=np.float64)
+        self._keep_rhs = (b, c)
+        _check(self._L.pdhg_batch_set_rhs(self._ctx, _ptr(b), _ptr(c)), allow_positive=False)
 
     def solve(self, eps_rel: float = 1e-4, max_iter: int = 1_000_000):
         st = np.zeros(self.count, dtype=np.int32)

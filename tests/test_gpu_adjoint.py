@@ -2,6 +2,8 @@
 against a dense least-squares reference, central finite differences with
 independent HiGHS re-solves, and the autograd Function.  Tolerance: 1e-4
 relative (the gradient target), 1e-6 against the dense reference."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -168,3 +170,52 @@ def test_adjoint_full_size_batch_sampled():
         A = lp.dense()
         gr = R.grad_b(A, Bset, 2.0 * (R.polish(A, lp.b, Bset) - targets[i]))
         assert rel(gbs[i], gr) < 1e-4, i
+
+
+def test_autograd_on_device_reuses_one_context():
+    """A BatchLP keeps A's context across calls: each forward sends new b, c
+    (pdhg_batch_set_rhs) and everything stays on the GPU.  Two calls with
+    different b give the solutions and gradients of fresh contexts (and of
+    the dense reference); a backward after the BatchLP solved another b is
+    refused."""
+    import torch
+    from paper_2603_03150_gb300.autograd import BatchLP, lp_solution
+    lps = [lpgen.planted_lp(200, 500, 5, seed=s) for s in range(3)]
+    st = dict(m=np.array([lp.m for lp in lps], np.int32), n=np.array([lp.n for lp in lps], np.int32),
+              row_ptr=np.concatenate([lp.row_ptr for lp in lps]),
+              col=np.concatenate([lp.col for lp in lps]), val=np.concatenate([lp.val for lp in lps]))
+    rng = np.random.default_rng(4)
+    b0 = np.concatenate([lp.b for lp in lps])
+    c0 = np.concatenate([lp.c for lp in lps])
+    # a second b inside range(A_B) of each LP: b + A_B v keeps the active set
+    b1 = np.concatenate([lp.b + lp.dense()[:, lp.x_star > 0] @ rng.uniform(-0.1, 0.1, int((lp.x_star > 0).sum()))
+                         for lp in lps])
+    t = torch.tensor(rng.uniform(0, 1, c0.size), device="cuda")
+    blp = BatchLP(st, device="cuda")
+    for bv in (b0, b1):
+        b = torch.tensor(bv, device="cuda", requires_grad=True)
+        c = torch.tensor(c0, device="cuda", requires_grad=True)
+        x = lp_solution(b, c, blp)
+        assert x.is_cuda
+        ((x - t) ** 2).sum().backward()
+        assert b.grad.is_cuda and torch.all(c.grad == 0)
+        mo = np.concatenate([[0], np.cumsum([lp.m for lp in lps])])
+        with solve_batch([dataclasses.replace(lp, b=bv[mo[i]:mo[i + 1]]) for i, lp in enumerate(lps)],
+                         precision="fp64") as s:
+            p = s.polish()
+        assert rel(x.detach().cpu().numpy(), np.asarray(p["x"])) < 1e-8
+        off, mo = 0, 0
+        for lp in lps:
+            xi = x.detach().cpu().numpy()[off:off + lp.n]
+            gr = R.grad_b(lp.dense(), xi > 0, 2.0 * (xi - t.cpu().numpy()[off:off + lp.n]))
+            assert rel(b.grad.cpu().numpy()[mo:mo + lp.m], gr) < 1e-6
+            off += lp.n
+            mo += lp.m
+    # two forwards on one BatchLP, then the first one's backward: refused
+    b = torch.tensor(b0, device="cuda", requires_grad=True)
+    c = torch.tensor(c0, device="cuda")
+    x1 = lp_solution(b, c, blp)
+    lp_solution(torch.tensor(b1, device="cuda"), c, blp)
+    with pytest.raises(RuntimeError):
+        x1.sum().backward()
+    blp.close()
