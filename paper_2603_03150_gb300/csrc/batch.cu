@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(BLOCK) k_bdual(BatchBuffers<T> B, int i) {
 template <typename T, int BLOCK>
 struct BEvalEpi {
   const T *x, *x_avg, *x_last;
-  const double *c_t, *D_c;
+  const double *c_t, *Dc_inv;
   const Scalars* sc;
   double* rec;
   double* red;
@@ -126,13 +126,13 @@ struct BEvalEpi {
     return true;
   }
   __device__ __forceinline__ void row(int j, const T (&s)[2], int) {
-    const double cj = c_t[j], dc = D_c[j];
+    const double cj = c_t[j], dci = Dc_inv[j];
     const double xl = (double)x_last[j];
     const double xs[2] = {(double)x[j], (double)x_avg[j]};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const double rd = fmin(0.0, cj - (double)s[c]);
-      const double ru = rd / dc;
+      const double ru = rd * dci;
       const double dx = xs[c] - xl;
       q[c][Q_S2] += rd * rd;
       q[c][Q_U2] += ru * ru;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(BLOCK) k_beval(BatchBuffers<T> B, int chunk) {
   __shared__ double red[kEvalQ * (BLOCK / 32)];
   __shared__ int is_last, active;
   const IterBuffers<T>& I = B.it;
-  BEvalEpi<T, BLOCK> epi{I.x, I.x_avg, I.x_last, I.c_t64, I.D_c, I.sc, B.rec_t, red, {}};
+  BEvalEpi<T, BLOCK> epi{I.x, I.x_avg, I.x_last, I.c_t64, I.Dc_inv, I.sc, B.rec_t, red, {}};
   Gather<T, 2> g{{I.y, I.y_avg}};
   run_sched<T, 2, BLOCK, E>(I.t_sched, I.t_rp, I.t_col, I.t_val, g, epi, smem);
   // m side over the row ranges of A's tiles (no products needed)
@@ -171,12 +171,12 @@ __global__ void __launch_bounds__(BLOCK) k_beval(BatchBuffers<T> B, int chunk) {
     for (int k = 0; k < kEvalQ; ++k) q[k] = 0.0;
     if (tl.split < 0 || tl.part == 0) {
       for (int i = tl.row_begin + threadIdx.x; i < tl.row_end; i += BLOCK) {
-        const double bi = I.b_t64[i], dr = I.D_r[i], yl = (double)I.y_last[i];
+        const double bi = I.b_t64[i], dri = I.Dr_inv[i], yl = (double)I.y_last[i];
         const double axs[2] = {(double)I.Ax[i], (double)I.Ax_avg[i]};
         const double ys[2] = {(double)I.y[i], (double)I.y_avg[i]};
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const double rp = bi - axs[c], ru = rp / dr, dy = ys[c] - yl;
+          const double rp = bi - axs[c], ru = rp * dri, dy = ys[c] - yl;
           q[c * Q_N + Q_S1] += rp * rp;
           q[c * Q_N + Q_U1] += ru * ru;
           q[c * Q_N + Q_S4] += bi * ys[c];
@@ -769,6 +769,8 @@ static BatchBuffers<T> batch_buffers(pdhg_ctx* ctx) {
   I.b_t64 = ctx->b_t64;
   I.D_r = ctx->D_r;
   I.D_c = ctx->D_c;
+  I.Dr_inv = ctx->Dr_inv;
+  I.Dc_inv = ctx->Dc_inv;
   I.sc = ctx->sc;
   I.m = ctx->m;
   I.n = ctx->n;

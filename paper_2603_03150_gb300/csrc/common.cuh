@@ -79,10 +79,10 @@ struct PanelView {
   const uint16_t* col;  // column within the panel
   const uint32_t* wd;   // window words, one per 8 nonzeros
   const int32_t* psrow; // row of each pseudo-row
-  float* partial;       // [npanels][rows]
+  float* partial;       // [npanels][pstride]: panel p's sums at p * pstride + row
   int32_t P, npanels, rows, cols, nblocks, ntiles;
   int32_t pscap;        // pseudo-rows of a tile at most (128 or 256): the staged sums per warp
-  int32_t pad;
+  int32_t pstride;      // rows rounded up to a multiple of 4 (16-byte aligned panels)
 };
 
 // ---------------------------------------------------------------------------

@@ -108,6 +108,7 @@ struct pdhg_ctx {
   // vectors
   double *b = nullptr, *c = nullptr, *b_t64 = nullptr, *c_t64 = nullptr, *D_r = nullptr,
          *D_c = nullptr;
+  double *Dr_inv = nullptr, *Dc_inv = nullptr;  // 1 / D_r, 1 / D_c (the evaluation multiplies)
   float *b_t32 = nullptr, *c_t32 = nullptr;
   void *x = nullptr, *y = nullptr, *x_avg = nullptr, *y_avg = nullptr, *x_last = nullptr,
        *y_last = nullptr, *Ax = nullptr, *Ax_avg = nullptr, *Ax_last = nullptr;

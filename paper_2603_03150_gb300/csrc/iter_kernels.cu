@@ -53,17 +53,17 @@ __global__ void __launch_bounds__(BLOCK) k_dual(IterBuffers<T> B, int i) {
 template <typename T>
 struct EvalEpi {
   const T *x, *x_avg, *x_last;
-  const double *c_t, *D_c;
+  const double *c_t, *Dc_inv;
   double* split_q;
   double q[2][Q_N];
   __device__ __forceinline__ void contrib(int j, const T (&s)[2], double (&o)[2][Q_N]) const {
-    const double cj = c_t[j], dc = D_c[j];
+    const double cj = c_t[j], dci = Dc_inv[j];
     const double xl = (double)x_last[j];
     const double xs[2] = {(double)x[j], (double)x_avg[j]};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const double rd = fmin(0.0, cj - (double)s[c]);
-      const double ru = rd / dc;
+      const double ru = rd * dci;
       const double dx = xs[c] - xl;
       o[c][Q_S2] = rd * rd;
       o[c][Q_U2] = ru * ru;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
   __shared__ double red[kEvalQ * (BLOCK / 32)];
   __shared__ double tot[kEvalQ];
   __shared__ int is_last;
-  EvalEpi<T> epi{B.x, B.x_avg, B.x_last, B.c_t64, B.D_c, B.split_q, {}};
+  EvalEpi<T> epi{B.x, B.x_avg, B.x_last, B.c_t64, B.Dc_inv, B.split_q, {}};
 #pragma unroll
   for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -115,13 +115,13 @@ __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
   run_sched<T, 2, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
   // m side: primal residual, dual objective, distance to the last restart point
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < B.m; i += gridDim.x * BLOCK) {
-    const double bi = B.b_t64[i], dr = B.D_r[i], yl = (double)B.y_last[i];
+    const double bi = B.b_t64[i], dri = B.Dr_inv[i], yl = (double)B.y_last[i];
     const double axs[2] = {(double)B.Ax[i], (double)B.Ax_avg[i]};
     const double ys[2] = {(double)B.y[i], (double)B.y_avg[i]};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const double rp = bi - axs[c];
-      const double ru = rp / dr;
+      const double ru = rp * dri;
       const double dy = ys[c] - yl;
       epi.q[c][Q_S1] += rp * rp;
       epi.q[c][Q_U1] += ru * ru;

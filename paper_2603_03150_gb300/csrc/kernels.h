@@ -27,6 +27,7 @@ struct IterBuffers {
   double rho;  // Halpern reflection
   const T *c_t, *b_t;                       // scaled c, b in precision T
   const double *c_t64, *b_t64, *D_r, *D_c;  // float64 copies and scalings
+  const double *Dr_inv, *Dc_inv;            // their reciprocals
   Scalars* sc;
   double* partials;    // [grid][kEvalQ]
   double* split_q;     // [split groups of A^T][kEvalQ]
@@ -134,6 +135,8 @@ void launch_row_stat(int nrows, const int32_t* rp, const int32_t* col, const dou
                      const double* d_self, const double* d_other, int mode, double* out,
                      const RowStatPlan& plan, cudaStream_t s);
 void launch_div(double* d, const double* r, int len, cudaStream_t s);
+// out[i] = 1 / in[i]
+void launch_recip(const double* in, double* out, int64_t len, cudaStream_t s);
 void launch_fill(double* d, double v, int64_t len, cudaStream_t s);
 // A~_ij = (D_r[i] A_ij) D_c[j]; transposed = 1 when the rows are columns of A
 void launch_scale_vals(int nrows, const int32_t* rp, const int32_t* col, const double* val,

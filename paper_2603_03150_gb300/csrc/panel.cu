@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   }
   __syncthreads();
   float* st = stage + warp * V.pscap;
-  float* part = V.partial + (size_t)bd.panel * V.rows;
+  float* part = V.partial + (size_t)bd.panel * V.pstride;
   while (t < bd.t_end) {
     const PanelTile tl = cur.tl;
     int t_next = -1;  // set once the next tile's loads are issued
@@ -251,45 +251,82 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   }
 }
 
-// Row pass: s_i = the sum of partial[p][i] over the panels, then the
-// half-step's row epilogue.  G consecutive lanes share a row: lane k adds
-// its contiguous share of the panels in order (8 loads in flight per round),
-// lane 0 adds the shares in lane order, so the order of the sum is fixed.
-// The row's epilogue operands are loaded before the partial sums arrive.
-// Warps stride over groups of 32 / G rows.
+// Row pass: s_i = the sum of partial[p][i] over the panels in panel order,
+// then the half-step's row epilogue.
+// G = 0 (up to 32 panels, rows enough for 4 per thread on every SM): a
+// thread takes 4 consecutive rows with 16-byte loads of each panel's 4 sums
+// and of the epilogue's operands (loaded before the sums arrive); rows past
+// the last multiple of 4 one per thread.
+// G >= 1: G consecutive lanes share a row: lane k adds its contiguous share
+// of the panels in order (8 loads in flight per round), lane 0 adds the
+// shares in lane order; warps stride over groups of 32 / G rows.
 template <int G, class Epi>
 __device__ __forceinline__ void panel_rows(const PanelView& V, Epi& epi) {
   const int rows = V.rows, np = V.npanels;
-  const int per = (np + G - 1) / G;  // panels of one lane
-  const int lane = threadIdx.x & 31, k = lane % G, base_lane = lane - k;
-  const int mine = max(0, min(per, np - k * per));
-  const size_t stride = (size_t)rows;
-  const float* __restrict__ part = V.partial + (size_t)(k * per) * stride;
-  constexpr int kRowsPerWarp = 32 / G;
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int r0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kRowsPerWarp; r0 < rows;
-       r0 += nw * kRowsPerWarp) {
-    const int i = r0 + lane / G;
-    const bool live = i < rows;
-    typename Epi::In in{};
-    if (live && k == 0) in = epi.load(i);
-    float t = 0.f;
-    const float* pp = part + i;
-    for (int c = 0; c < mine; c += 8) {
-      float q[8];
+  const size_t stride = (size_t)V.pstride;
+  if constexpr (G == 0) {
+    const int nthr = gridDim.x * blockDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n4 = rows >> 2;
+    for (int q = tid; q < n4; q += nthr) {
+      const int i = q << 2;
+      const typename Epi::In4 in = epi.load4(i);
+      const float* pp = V.partial + i;
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int c = 0; c < np; c += 8) {
+        float4 u[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) q[r] = (live && c + r < mine) ? __ldcg(pp + (c + r) * stride) : 0.f;
+        for (int r = 0; r < 8; ++r)
+          u[r] = c + r < np ? __ldcg(reinterpret_cast<const float4*>(pp + (size_t)(c + r) * stride))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        if (c + r < mine) t += q[r];
+        for (int r = 0; r < 8; ++r)
+          if (c + r < np) {
+            t.x += u[r].x;
+            t.y += u[r].y;
+            t.z += u[r].z;
+            t.w += u[r].w;
+          }
+      }
+      epi.apply4(i, in, t);
     }
-    float s = t;
-#pragma unroll
-    for (int o = 1; o < G; ++o) {
-      const float u = __shfl_sync(0xffffffffu, t, base_lane + o);
-      if (k == 0) s += u;
+    for (int i = (n4 << 2) + tid; i < rows; i += nthr) {
+      const typename Epi::In in = epi.load(i);
+      float t = 0.f;
+      for (int c = 0; c < np; ++c) t += __ldcg(V.partial + (size_t)c * stride + i);
+      epi.apply(i, in, t);
     }
-    if (live && k == 0) epi.apply(i, in, s);
+  } else {
+    const int per = (np + G - 1) / G;  // panels of one lane
+    const int lane = threadIdx.x & 31, k = lane % G, base_lane = lane - k;
+    const int mine = max(0, min(per, np - k * per));
+    const float* __restrict__ part = V.partial + (size_t)(k * per) * stride;
+    constexpr int kRowsPerWarp = 32 / G;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int r0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kRowsPerWarp; r0 < rows;
+         r0 += nw * kRowsPerWarp) {
+      const int i = r0 + lane / G;
+      const bool live = i < rows;
+      typename Epi::In in{};
+      if (live && k == 0) in = epi.load(i);
+      float t = 0.f;
+      const float* pp = part + i;
+      for (int c = 0; c < mine; c += 8) {
+        float q[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) q[r] = (live && c + r < mine) ? __ldcg(pp + (c + r) * stride) : 0.f;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          if (c + r < mine) t += q[r];
+      }
+      float s = t;
+#pragma unroll
+      for (int o = 1; o < G; ++o) {
+        const float u = __shfl_sync(0xffffffffu, t, base_lane + o);
+        if (k == 0) s += u;
+      }
+      if (live && k == 0) epi.apply(i, in, s);
+    }
   }
 }
 
@@ -364,8 +401,19 @@ int panel_lanes(int np) {
   return g;
 }
 
+// lanes per row of the row pass, 0 for 4 rows per thread: with up to 32 panels
+// and at least 2^19 rows (enough threads to fill every SM at 4 rows each)
+int row_lanes(int rows, int np) {
+  const int g = panel_lanes(np);
+  return g == 1 && rows >= (1 << 19) ? 0 : g;
+}
+
 #define PDHG_DISPATCH_G(g, ...)      \
   switch (g) {                       \
+    case 0: {                        \
+      constexpr int G_ = 0;          \
+      __VA_ARGS__;                   \
+    } break;                         \
     case 1: {                        \
       constexpr int G_ = 1;          \
       __VA_ARGS__;                   \
@@ -403,7 +451,7 @@ void launch_panel_half(const IterBuffers<float>& B, const PanelView& V, bool dua
   launch_pdl(k_panel_spmv, V.nblocks, kPanelThreads, panel_smem(V.P, V.pscap), s, V, v,
              (const Scalars*)B.sc);
   if (between) cudaEventRecordWithFlags(between, s, cudaEventRecordExternal);
-  const int g = panel_lanes(V.npanels);
+  const int g = row_lanes(V.rows, V.npanels);
   if (dual && method == 1) {
     PDHG_DISPATCH_G(g, launch_pdl(k_panel_hdual<G_>, row_grid, 256, 0, s, B, V, i));
   } else if (dual) {
@@ -423,7 +471,8 @@ void launch_panel_spmv_only(const IterBuffers<float>& B, const PanelView& V, boo
 }
 
 int panel_row_grid(int rows, int npanels, int nsm) {
-  const int64_t threads = (int64_t)rows * panel_lanes(npanels);
+  const int g = row_lanes(rows, npanels);
+  const int64_t threads = g == 0 ? ((int64_t)rows + 3) / 4 : (int64_t)rows * g;
   return (int)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, (int64_t)nsm * 6));
 }
 
@@ -661,6 +710,7 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   const int32_t* col = on_a ? ctx->a_col : ctx->t_col;
   const float* val = on_a ? ctx->a_val32 : ctx->t_val32;
   int64_t len = (int64_t)np * R;  // the 256 cap gives the narrowest panels: the most of them
+  const int pstride = (R + 3) & ~3;
 
   // pseudo-rows: counts per (panel, row), their prefix, the first of each panel
   Tmp<int32_t> cnt, src, flag, psidx, scan_tmp, pfirst;
@@ -821,8 +871,8 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   if (nb > 0)
     PL_CK(cudaMemcpyAsync(out->blocks, h_blocks.data(), sizeof(PanelBlock) * nb,
                           cudaMemcpyHostToDevice, s));
-  CKS(dalloc(ctx, &out->partial, (size_t)len));
-  PL_CK(cudaMemsetAsync(out->partial, 0, sizeof(float) * len, s));
+  CKS(dalloc(ctx, &out->partial, (size_t)np * pstride));
+  PL_CK(cudaMemsetAsync(out->partial, 0, sizeof(float) * (size_t)np * pstride, s));
   PL_CK(cudaStreamSynchronize(s));  // the host vectors above go out of scope
   PL_CK(cudaGetLastError());
 
@@ -841,6 +891,7 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   V.nblocks = nb;
   V.ntiles = nt;
   V.pscap = pscap;
+  V.pstride = pstride;
   out->pseudo_rows = nps;
   out->nnz_padded = nzp;
   out->on = nb > 0;

@@ -1,5 +1,6 @@
 // Set-up kernels: CSR validation, stable transpose, diagonal scaling (Ruiz and
 // Pock-Chambolle statistics), scaled copies, reductions and power iteration.
+#include <algorithm>
 #include <math.h>
 
 #include "kernels.h"
@@ -553,6 +554,16 @@ __global__ void k_init_scalars(Scalars* sc, const double* sums, const PowerState
   sc->kkt_last = sqrt(w2 * sums[2] + sums[4] / w2);
   sc->kkt_prev = sc->kkt_last;
 }
+__global__ void k_recip(const double* __restrict__ in, double* out, int64_t len) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 1.0 / in[i];
+}
+void launch_recip(const double* in, double* out, int64_t len, cudaStream_t s) {
+  const int64_t g = std::min<int64_t>(std::max<int64_t>((len + 255) / 256, 1), 4096);
+  k_recip<<<(int)g, 256, 0, s>>>(in, out, len);
+}
+
 void launch_init_scalars(Scalars* sc, const double* sums, const PowerState* ps, double eta_safety,
                          cudaStream_t s) {
   k_init_scalars<<<1, 32, 0, s>>>(sc, sums, ps, eta_safety);

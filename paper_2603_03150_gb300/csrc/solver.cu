@@ -255,6 +255,8 @@ static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
   B.b_t64 = ctx->b_t64;
   B.D_r = ctx->D_r;
   B.D_c = ctx->D_c;
+  B.Dr_inv = ctx->Dr_inv;
+  B.Dc_inv = ctx->Dc_inv;
   B.sc = ctx->sc;
   B.partials = ctx->partials;
   B.split_q = ctx->split_q;
@@ -644,6 +646,8 @@ pdhg_status pdhg::alloc_arrays(pdhg_ctx* ctx) {
   CKS(dalloc(ctx, &ctx->c_t64, n));
   CKS(dalloc(ctx, &ctx->D_r, m));
   CKS(dalloc(ctx, &ctx->D_c, n));
+  CKS(dalloc(ctx, &ctx->Dr_inv, m));
+  CKS(dalloc(ctx, &ctx->Dc_inv, n));
   const size_t es = elem(ctx);
   void** vecs_n[] = {&ctx->x, &ctx->x_avg, &ctx->x_last};
   void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg, &ctx->Ax_last};
@@ -793,6 +797,9 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
                     ctx->t_val64, ctx->t_val32, ctx->stream);
   launch_scale_vec(m, ctx->D_r, ctx->b, ctx->b_t64, ctx->b_t32, ctx->stream);
   launch_scale_vec(n, ctx->D_c, ctx->c, ctx->c_t64, ctx->c_t32, ctx->stream);
+  launch_recip(ctx->D_r, ctx->Dr_inv, m, ctx->stream);
+  launch_recip(ctx->D_c, ctx->Dc_inv, n, ctx->stream);
+  ctx->launches += 2;
   ctx->launches += 2 + 4LL * rounds + 4 +
                    (long long)rounds * ((plan_a.nlong > 0) + (plan_t.nlong > 0));
   CK(cudaGetLastError());
