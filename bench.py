@@ -472,27 +472,31 @@ def run_batch(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), out
 
-    def batched(precision, from_host=False):
+    def batched(precision, from_host=False, persistent=0):
         if from_host:
             s = pdhg.BatchSolver(lps, precision=precision)
         else:
-            s = pdhg.BatchSolver(arrays=dev_arrays, precision=precision, device_io=True)
+            s = pdhg.BatchSolver(arrays=dev_arrays, precision=precision, device_io=True,
+                                 persistent=persistent)
         st = s.solve(EPS, args.max_iter)
         g = s.get()
+        n_launch = s.launch_count()
         s.close()
-        return st, g
+        return st, g, n_launch
 
     res = {}
-    for prec in ("fp32", "fp64"):
+    # graph of per-half-step launches (default) and one persistent cooperative launch
+    for prec, persistent in (("fp32", 0), ("fp64", 0), ("fp32", 1), ("fp64", 1)):
         for _ in range(max(1, args.warmup - 2)):
-            batched(prec)
+            batched(prec, persistent=persistent)
         ms = []
         for _ in range(args.steps):
-            t, (st, g) = timed(lambda: batched(prec))
+            t, (st, g, nl) = timed(lambda: batched(prec, persistent=persistent))
             ms.append(t)
-        res[prec] = dict(ms=float(np.mean(ms)), status=int(st),
-                         iters_max=int(g["iters"].max()), iters_median=int(np.median(g["iters"])),
-                         max_violation_max=float(g["max_violation"].max()))
+        res[prec + ("_persistent" if persistent else "")] = dict(
+            ms=float(np.mean(ms)), status=int(st), iters_max=int(g["iters"].max()),
+            iters_median=int(np.median(g["iters"])),
+            max_violation_max=float(g["max_violation"].max()), kernel_launches=int(nl))
 
     def sequential():
         it = []
@@ -524,6 +528,9 @@ def run_batch(args):
                         "from": "Python LP objects on the host (concatenation and upload timed)",
                         "ms_per_step": round(e2e_ms, 2)},
                 "batched_fp32": res["fp32"], "batched_fp64": res["fp64"],
+                "batched_fp32_persistent": res["fp32_persistent"],
+                "batched_fp64_persistent": res["fp64_persistent"],
+                "persistent_vs_graph_fp32_speedup": round(res["fp32"]["ms"] / res["fp32_persistent"]["ms"], 3),
                 "sequential_fp64_ms": round(t_seq, 2),
                 "sequential_fp64_iters_median": int(np.median(seq_it)),
                 "batched_fp64_vs_sequential_fp64_speedup": round(t_seq / res["fp64"]["ms"], 2),

@@ -125,6 +125,18 @@ typedef struct pdhg_options {
   double pid_kp;           /* proportional gain (default 0.99)                  */
   double pid_ki;           /* integral gain (default 0.01)                      */
   double pid_kd;           /* derivative gain (default 0)                       */
+  int32_t persistent;      /* batched contexts: 0 (default): each F-iteration
+                              chunk is a CUDA graph of per-half-step launches;
+                              1: the whole solve is one cooperative launch
+                              (every block resident), the phases separated by
+                              grid-wide barriers whose waits are bounded; it
+                              runs the SpMV schedules of 8 nonzeros per thread
+                              (full tiles) whatever the tuner picked           */
+  int32_t wait_limit_ms;   /* bound of one grid-barrier wait (default 1000); a
+                              wait past it ends the solve with PDHG_TIMEOUT   */
+  int32_t wait_test;       /* 1: every grid barrier waits for one arrival more
+                              than the grid has, so the bounded wait runs out
+                              (tests the PDHG_TIMEOUT path; default 0)        */
 } pdhg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -311,7 +323,11 @@ pdhg_status pdhg_batch_set_rhs(pdhg_ctx* ctx, const double* b, const double* c);
  * passed the Section 2 test with eps_rel or the iteration count reaches
  * max_iter.  lp_status (HOST int32[count] or NULL) receives each LP's
  * status; the return value is the largest of them (PDHG_CONVERGED only if
- * all converged).  */
+ * all converged).  With options.persistent = 1 the solve is one cooperative
+ * launch; if one of its grid barriers waits past options.wait_limit_ms every
+ * block returns and the call returns PDHG_TIMEOUT (every lp_status too): the
+ * iterates are then not meaningful, the context stays usable (destroy it, or
+ * restore a state before solving again).  */
 pdhg_status pdhg_batch_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_iter,
                              int32_t* lp_status);
 

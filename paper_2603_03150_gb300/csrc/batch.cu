@@ -90,20 +90,32 @@ struct BDualEpi {
   }
 };
 
+// Kernel bodies are device functions: the per-half-step kernels below run
+// one each, the persistent kernel (k_bpersist) runs them all in turn.
 template <typename T, int BLOCK, int E>
-__global__ void __launch_bounds__(BLOCK) k_bprimal(BatchBuffers<T> B, int i) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void bprimal_body(const BatchBuffers<T>& B, int i, unsigned char* smem) {
   BPrimalEpi<T> epi{B.it.x, B.it.c_t, B.it.x_avg, B.it.sc, i, T(0), T(0), false};
   Gather<T, 1> g{{B.it.y}};
   run_sched<T, 1, BLOCK, E>(B.it.t_sched, B.it.t_rp, B.it.t_col, B.it.t_val, g, epi, smem);
 }
 
 template <typename T, int BLOCK, int E>
-__global__ void __launch_bounds__(BLOCK) k_bdual(BatchBuffers<T> B, int i) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void bdual_body(const BatchBuffers<T>& B, int i, unsigned char* smem) {
   BDualEpi<T> epi{B.it.y, B.it.b_t, B.it.Ax, B.it.y_avg, B.it.Ax_avg, B.it.sc, i, T(0), T(0), false};
   Gather<T, 1> g{{B.it.x}};
   run_sched<T, 1, BLOCK, E>(B.it.a_sched, B.it.a_rp, B.it.a_col, B.it.a_val, g, epi, smem);
+}
+
+template <typename T, int BLOCK, int E>
+__global__ void __launch_bounds__(BLOCK) k_bprimal(BatchBuffers<T> B, int i) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bprimal_body<T, BLOCK, E>(B, i, smem);
+}
+
+template <typename T, int BLOCK, int E>
+__global__ void __launch_bounds__(BLOCK) k_bdual(BatchBuffers<T> B, int i) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bdual_body<T, BLOCK, E>(B, i, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -154,8 +166,7 @@ struct BEvalEpi {
 };
 
 template <typename T, int BLOCK, int E>
-__global__ void __launch_bounds__(BLOCK) k_beval(BatchBuffers<T> B, int chunk) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void beval_body(const BatchBuffers<T>& B, int chunk, unsigned char* smem) {
   __shared__ double red[kEvalQ * (BLOCK / 32)];
   __shared__ int is_last, active;
   const IterBuffers<T>& I = B.it;
@@ -224,9 +235,15 @@ __global__ void __launch_bounds__(BLOCK) k_beval(BatchBuffers<T> B, int chunk) {
   }
 }
 
+template <typename T, int BLOCK, int E>
+__global__ void __launch_bounds__(BLOCK) k_beval(BatchBuffers<T> B, int chunk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  beval_body<T, BLOCK, E>(B, chunk, smem);
+}
+
 // restart of the LPs whose rule fired: candidate -> iterate and last point
 template <typename T>
-__global__ void k_brestart(BatchBuffers<T> B) {
+__device__ __forceinline__ void brestart_body(const BatchBuffers<T>& B) {
   const IterBuffers<T>& I = B.it;
   for (int t = blockIdx.x; t < I.t_sched.ntiles; t += gridDim.x) {
     const Tile tl = I.t_sched.tiles[t];
@@ -259,6 +276,11 @@ __global__ void k_brestart(BatchBuffers<T> B) {
       }
     }
   }
+}
+
+template <typename T>
+__global__ void k_brestart(BatchBuffers<T> B) {
+  brestart_body<T>(B);
 }
 
 // ---------------------------------------------------------------------------
@@ -428,8 +450,10 @@ __global__ void k_binit(Scalars* sc, const PowerState* ps, const int64_t* m_off,
 // checking = true: only the LPs with a pending float64 check, their screened
 // candidate
 template <typename T>
-__global__ void k_bchoose(SchedView Sn, SchedView Sm, const Scalars* sc, const T* x, const T* x_avg,
-                          const T* y, const T* y_avg, double* xs, double* ys, bool checking) {
+__device__ __forceinline__ void bchoose_body(const SchedView& Sn, const SchedView& Sm,
+                                             const Scalars* sc, const T* x, const T* x_avg,
+                                             const T* y, const T* y_avg, double* xs, double* ys,
+                                             bool checking) {
   for (int t = blockIdx.x; t < Sn.ntiles; t += gridDim.x) {
     const Tile tl = Sn.tiles[t];
     if (tl.split >= 0 && tl.part != 0) continue;
@@ -448,6 +472,12 @@ __global__ void k_bchoose(SchedView Sn, SchedView Sm, const Scalars* sc, const T
     for (int i = tl.row_begin + threadIdx.x; i < tl.row_end; i += blockDim.x)
       ys[i] = (double)(avg ? y_avg[i] : y[i]);
   }
+}
+
+template <typename T>
+__global__ void k_bchoose(SchedView Sn, SchedView Sm, const Scalars* sc, const T* x, const T* x_avg,
+                          const T* y, const T* y_avg, double* xs, double* ys, bool checking) {
+  bchoose_body<T>(Sn, Sm, sc, x, x_avg, y, y_avg, xs, ys, checking);
 }
 
 // gate (optional): only the tiles of LPs with a pending float64 check
@@ -531,16 +561,36 @@ struct BRepMEpi {
 };
 
 template <int BLOCK>
+__device__ __forceinline__ void brep_n_body(const SchedView& S, const int32_t* rp, const int32_t* col,
+                                            const double* val, const double* x_s, const double* y_s,
+                                            const double* c_t, const double* D_c, double* x_out,
+                                            double* z_out, double* rec, const Scalars* gate,
+                                            unsigned char* smem) {
+  __shared__ double red[3 * (BLOCK / 32)];
+  BRepNEpi<BLOCK> epi{x_s, c_t, D_c, x_out, z_out, rec, red, gate, 0, 0, 0, 0};
+  Gather<double, 1> g{{y_s}};
+  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void brep_m_body(const SchedView& S, const int32_t* rp, const int32_t* col,
+                                            const double* val, const double* x_s, const double* y_s,
+                                            const double* b_t, const double* D_r, double* y_out,
+                                            double* rec, const Scalars* gate, unsigned char* smem) {
+  __shared__ double red[2 * (BLOCK / 32)];
+  BRepMEpi<BLOCK> epi{y_s, b_t, D_r, y_out, rec, red, gate, 0, 0, 0};
+  Gather<double, 1> g{{x_s}};
+  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
+}
+
+template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_brep_n(SchedView S, const int32_t* rp, const int32_t* col,
                                                  const double* val, const double* x_s,
                                                  const double* y_s, const double* c_t,
                                                  const double* D_c, double* x_out, double* z_out,
                                                  double* rec, const Scalars* gate) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[3 * (BLOCK / 32)];
-  BRepNEpi<BLOCK> epi{x_s, c_t, D_c, x_out, z_out, rec, red, gate, 0, 0, 0, 0};
-  Gather<double, 1> g{{y_s}};
-  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
+  brep_n_body<BLOCK>(S, rp, col, val, x_s, y_s, c_t, D_c, x_out, z_out, rec, gate, smem);
 }
 
 template <int BLOCK>
@@ -550,10 +600,7 @@ __global__ void __launch_bounds__(BLOCK) k_brep_m(SchedView S, const int32_t* rp
                                                  const double* D_r, double* y_out, double* rec,
                                                  const Scalars* gate) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[2 * (BLOCK / 32)];
-  BRepMEpi<BLOCK> epi{y_s, b_t, D_r, y_out, rec, red, gate, 0, 0, 0};
-  Gather<double, 1> g{{x_s}};
-  run_tiles<double, 1, BLOCK, kFixedE>(S, rp, col, val, g, epi, smem);
+  brep_m_body<BLOCK>(S, rp, col, val, x_s, y_s, b_t, D_r, y_out, rec, gate, smem);
 }
 
 // out[l][8] = {r_P, r_D, gap, max violation, c^T x, b^T y, x^T z, 0}
@@ -586,8 +633,9 @@ __global__ void k_brep_final(const double* rec_n, const int32_t* lp_n, const dou
 
 // Float64 check of each LP whose screen passed: the Section 2 test at eps on
 // its report records; an LP that passes is finished (one fewer active LP)
-__global__ void k_bfp64_final(const double* rec_n, const int32_t* lp_n, const double* rec_m,
-                              const int32_t* lp_m, int count, Scalars* sc, int32_t* ctl) {
+__device__ __forceinline__ void bfp64_final_body(const double* rec_n, const int32_t* lp_n,
+                                                 const double* rec_m, const int32_t* lp_m, int count,
+                                                 Scalars* sc, int32_t* ctl) {
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
     Scalars& s = sc[l];
     if (!s.verify) continue;
@@ -603,6 +651,11 @@ __global__ void k_bfp64_final(const double* rec_n, const int32_t* lp_n, const do
     eval_fp64_check(s, u1, u2, s3, s4, nullptr, nullptr, nullptr);
     if (s.done) atomicSub(ctl, 1);
   }
+}
+
+__global__ void k_bfp64_final(const double* rec_n, const int32_t* lp_n, const double* rec_m,
+                              const int32_t* lp_m, int count, Scalars* sc, int32_t* ctl) {
+  bfp64_final_body(rec_n, lp_n, rec_m, lp_m, count, sc, ctl);
 }
 
 // Algorithm 1 per LP: z~ = max(0, c~ - A~^T y~) and x~^T z~ per tile
@@ -720,6 +773,10 @@ static cudaError_t configure_batch_e(size_t mx) {
   return e;
 }
 
+struct PersistArgs;
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 1) k_bpersist(BatchBuffers<T> B, PersistArgs P);
+
 static cudaError_t configure_batch_kernels(size_t mx) {
   cudaError_t e = configure_batch_e<8>(mx);
   if (e == cudaSuccess) e = configure_batch_e<32>(mx);
@@ -728,7 +785,8 @@ static cudaError_t configure_batch_kernels(size_t mx) {
   if (e == cudaSuccess) e = configure_batch_e<-8>(mx);
   for (const void* f : {(const void*)k_bpow_Av<kBlock>, (const void*)k_bpow_ATu<kBlock>,
                         (const void*)k_brep_n<kBlock>, (const void*)k_brep_m<kBlock>,
-                        (const void*)k_bws_z<kBlock>}) {
+                        (const void*)k_bws_z<kBlock>, (const void*)k_bpersist<float>,
+                        (const void*)k_bpersist<double>}) {
     cudaError_t r = set_max_dyn_smem(f, mx);
     if (r != cudaSuccess) e = r;
   }
@@ -822,6 +880,175 @@ void enqueue_batch_chunk(pdhg_ctx* ctx, int len) {
     enqueue_bchunk<float>(ctx, len);
   else
     enqueue_bchunk<double>(ctx, len);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched solve: one cooperative launch runs every chunk (the
+// half-steps, the evaluation, the float64 check and the restart) with a
+// grid-wide barrier between phases.  Each barrier's wait is bounded: past the
+// limit the block records a timeout and every block returns at its next
+// barrier, so the host reads PDHG_TIMEOUT instead of waiting on a hang.
+// ---------------------------------------------------------------------------
+struct GridSync {
+  unsigned int count, gen;
+  int err;    // 1: a barrier's wait ran past its limit
+  int extra;  // arrivals a barrier waits for beyond the grid: 0 (1 tests the bounded wait)
+};
+
+struct PersistArgs {
+  GridSync* gs;
+  unsigned long long limit_ns;
+  long long k0, max_iter;
+  int eval_freq;
+  // the float64 check of screened float32-mixed candidates
+  SchedView st8, sa8;
+  const double *t_val64, *a_val64;
+  double *xs64, *ys64;
+  const int32_t *lp_t8, *lp_a8;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// false in every thread of the block once any block's wait ran past limit_ns
+__device__ __forceinline__ bool grid_barrier(GridSync* g, unsigned long long limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &g->gen;
+    volatile int* verr = &g->err;
+    const unsigned int gen0 = *vgen;  // read before arriving: only the last arrival moves it
+    const unsigned int want = gridDim.x + (unsigned int)g->extra;
+    __threadfence();
+    int res = 1;
+    if (atomicAdd(&g->count, 1u) == want - 1u) {
+      atomicExch(&g->count, 0u);
+      __threadfence();
+      atomicAdd(&g->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == gen0) {
+        if (*verr != 0) {
+          res = 0;
+          break;
+        }
+        if (global_ns() - t0 > limit_ns) {
+          atomicExch(&g->err, 1);
+          res = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = res && *verr == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 1) k_bpersist(BatchBuffers<T> B, PersistArgs P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const IterBuffers<T>& I = B.it;
+  const long long F = P.eval_freq;
+  long long k = P.k0;
+  while (k < P.max_iter) {
+    const long long next = min((k / F + 1) * F, P.max_iter);
+    const int len = (int)(next - k);
+    for (int i = 0; i < len; ++i) {
+      bprimal_body<T, kBlock, kFixedE>(B, i, smem);
+      if (!grid_barrier(P.gs, P.limit_ns)) return;
+      bdual_body<T, kBlock, kFixedE>(B, i, smem);
+      if (!grid_barrier(P.gs, P.limit_ns)) return;
+    }
+    beval_body<T, kBlock, kFixedE>(B, len, smem);
+    if (!grid_barrier(P.gs, P.limit_ns)) return;
+    if constexpr (sizeof(T) == 4) {
+      bchoose_body<T>(P.st8, P.sa8, I.sc, I.x, I.x_avg, I.y, I.y_avg, P.xs64, P.ys64, true);
+      if (!grid_barrier(P.gs, P.limit_ns)) return;
+      brep_n_body<kBlock>(P.st8, I.t_rp, I.t_col, P.t_val64, P.xs64, P.ys64, I.c_t64, I.D_c,
+                          nullptr, nullptr, B.rec_t, I.sc, smem);
+      brep_m_body<kBlock>(P.sa8, I.a_rp, I.a_col, P.a_val64, P.xs64, P.ys64, I.b_t64, I.D_r,
+                          nullptr, B.rec_a, I.sc, smem);
+      if (!grid_barrier(P.gs, P.limit_ns)) return;
+      bfp64_final_body(B.rec_t, P.lp_t8, B.rec_a, P.lp_a8, B.count, I.sc, B.ctl);
+      if (!grid_barrier(P.gs, P.limit_ns)) return;
+    }
+    brestart_body<T>(B);
+    if (!grid_barrier(P.gs, P.limit_ns)) return;
+    k = next;
+    if (*reinterpret_cast<volatile int32_t*>(B.ctl) == 0) break;  // every LP has finished
+  }
+}
+
+// shared memory of the persistent kernel: its iteration and evaluation phases
+// on the fixed E = 8 schedules (one or two gathered vectors in the iteration
+// precision) and the float64 report passes
+static size_t persist_smem(const pdhg_ctx* ctx) {
+  const SchedView &A = ctx->sa8.view, &T = ctx->st8.view;
+  const bool mx = ctx->mixed;
+  return std::max({smem_for(0, mx, A.max_rows, A.e), smem_for(0, mx, T.max_rows, T.e),
+                   smem_for(1, mx, T.max_rows, T.e), ctx->l_t64.smem, ctx->l_a64.smem});
+}
+
+// the whole solve from iteration k0 to max_iter in one cooperative launch
+template <typename T>
+static pdhg_status persistent_solve(pdhg_ctx* ctx, long long k0, long long max_iter) {
+  const GridSync g{0u, 0u, 0, ctx->opt.wait_test ? 1 : 0};
+  CK(cudaMemcpyAsync(ctx->gsync, &g, sizeof(g), cudaMemcpyHostToDevice, ctx->stream));
+  // every phase on the fixed E = 8 schedules (the per-LP tile ranges with them)
+  BatchBuffers<T> B = batch_buffers<T>(ctx);
+  B.it.a_sched = ctx->sa8.view;
+  B.it.t_sched = ctx->st8.view;
+  B.lp_a_tiles = ctx->lp_a8_tiles;
+  B.lp_t_tiles = ctx->lp_t8_tiles;
+  PersistArgs P{};
+  P.gs = static_cast<GridSync*>(ctx->gsync);
+  P.limit_ns = (unsigned long long)ctx->opt.wait_limit_ms * 1000000ull;
+  P.k0 = k0;
+  P.max_iter = max_iter;
+  P.eval_freq = ctx->opt.eval_freq;
+  P.st8 = ctx->st8.view;
+  P.sa8 = ctx->sa8.view;
+  P.t_val64 = ctx->t_val64;
+  P.a_val64 = ctx->a_val64;
+  P.xs64 = ctx->xs64;
+  P.ys64 = ctx->ys64;
+  P.lp_t8 = ctx->lp_t8_tiles;
+  P.lp_a8 = ctx->lp_a8_tiles;
+  const size_t smem = persist_smem(ctx);
+  const void* f = reinterpret_cast<const void*>(k_bpersist<T>);
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bpersist<T>, kBlock, smem));
+  if (per_sm < 1) {
+    set_error("persistent batched solve: the kernel does not fit on an SM (%zu bytes of shared memory)",
+              smem);
+    return PDHG_CUDA_ERROR;
+  }
+  const int grid = per_sm * ctx->nsm;
+  void* args[] = {&B, &P};
+  CK(cudaLaunchCooperativeKernel(f, grid, kBlock, args, smem, ctx->stream));
+  ctx->launches += 1;
+  GridSync out{};
+  CK(cudaMemcpyAsync(&out, ctx->gsync, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  if (out.err) {
+    set_error("persistent batched solve: a grid barrier waited longer than %d ms; the iterates "
+              "are not meaningful",
+              ctx->opt.wait_limit_ms);
+    return PDHG_TIMEOUT;
+  }
+  return PDHG_OK;
+}
+
+pdhg_status batch_persistent_solve(pdhg_ctx* ctx, long long k0, long long max_iter) {
+  return ctx->mixed ? persistent_solve<float>(ctx, k0, max_iter)
+                    : persistent_solve<double>(ctx, k0, max_iter);
 }
 
 }  // namespace pdhg
@@ -1088,7 +1315,12 @@ static pdhg_status batch_create_impl(pdhg_ctx* ctx, const int32_t* m, const int3
   ctx->rec_tiles = std::max({A.ntiles, T.ntiles, A8.ntiles, T8.ntiles, 1});
   CKS(dalloc(ctx, &ctx->rec_t, (size_t)ctx->rec_tiles * kEvalQ));
   CKS(dalloc(ctx, &ctx->rec_a, (size_t)ctx->rec_tiles * kEvalQ));
-  CKS(dalloc(ctx, &ctx->active, 5));  // [4]: pdhg_batch_set_rhs's finiteness flag
+  CKS(dalloc(ctx, &ctx->active, 5));
+  {
+    int32_t* g = nullptr;  // the persistent solve's grid-barrier state (4 words)
+    CKS(dalloc(ctx, &g, 4));
+    ctx->gsync = g;
+  }  // [4]: pdhg_batch_set_rhs's finiteness flag
   CKS(dalloc(ctx, &ctx->breport, (size_t)count * 8));
   CK(cudaMemsetAsync(ctx->active, 0, 4 * sizeof(int32_t), ctx->stream));
 
@@ -1168,8 +1400,11 @@ extern "C" pdhg_status pdhg_batch_create(pdhg_ctx** out, int32_t count, const in
   if (ctx->opt.eval_freq < 1 ||
       (ctx->opt.precision != PDHG_FP64 && ctx->opt.precision != PDHG_FP32_MIXED) ||
       ctx->opt.method != 0 || !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6) ||
-      (ctx->opt.omega_rule != 0 && ctx->opt.omega_rule != 1)) {
+      (ctx->opt.omega_rule != 0 && ctx->opt.omega_rule != 1) ||
+      (ctx->opt.persistent != 0 && ctx->opt.persistent != 1) || ctx->opt.wait_limit_ms < 1 ||
+      (ctx->opt.wait_test != 0 && ctx->opt.wait_test != 1)) {
     set_error("invalid options (eval_freq >= 1, precision 0/1, 1 <= fp32_screen <= 1e6, "
+              "omega_rule 0/1, persistent 0/1, wait_limit_ms >= 1, wait_test 0/1, "
               "method 0: batched solves use the averaged iteration)");
     delete ctx;
     return PDHG_INVALID_ARG;
@@ -1285,7 +1520,21 @@ extern "C" pdhg_status pdhg_batch_solve(pdhg_ctx* ctx, double eps_rel, int64_t m
   CK(cudaMemcpyAsync(ctx->sc, hs.data(), sizeof(Scalars) * count, cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(cudaMemsetAsync(ctx->active, 0, 4 * sizeof(int32_t), ctx->stream));
-  if (ctx->opt.use_graphs) CKS(build_batch_graphs(ctx));
+  if (ctx->opt.persistent) {
+    // the active count the kernel polls starts at every LP
+    const int32_t all = count;
+    CK(cudaMemcpyAsync(ctx->active, &all, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    const pdhg_status ps = batch_persistent_solve(ctx, k, max_iter);
+    if (ps != PDHG_OK) {
+      ctx->last_status = ps;
+      ctx->report_valid = false;
+      if (lp_status)
+        for (int l = 0; l < count; ++l) lp_status[l] = ps;
+      return ps;
+    }
+    k = max_iter;  // the kernel ran to the end (or until every LP finished)
+  }
+  if (!ctx->opt.persistent && ctx->opt.use_graphs) CKS(build_batch_graphs(ctx));
   const long long F = ctx->opt.eval_freq;
   // pinned status words (the context's pinned status buffers are large enough)
   int32_t* h_ctl[2] = {reinterpret_cast<int32_t*>(ctx->h_sc[0]),

@@ -133,6 +133,7 @@ struct pdhg_ctx {
   int rec_tiles = 0;                          // tiles the record arrays hold
   int32_t* active = nullptr;                  // LPs not finished after the last evaluation
   int64_t *d_m_off = nullptr, *d_n_off = nullptr;  // [count + 1] row / column offsets (device)
+  void* gsync = nullptr;                      // grid-barrier state of the persistent batched solve
   double* breport = nullptr;                  // [count][8] per-LP report
   void* adjoint = nullptr;                    // active-set polish / adjoint buffers
   // schedules and launch shapes
@@ -213,5 +214,8 @@ pdhg_status polling_resources(pdhg_ctx* ctx);
 // twice the nonzeros); the device layout
 bool panel_shape(const pdhg_ctx* ctx, bool on_a, int* P, int* npanels, int pscap = 256);
 pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out);
+// batched solve from iteration k0 to max_iter in one cooperative launch
+// (PDHG_TIMEOUT if a grid barrier's bounded wait ran out)
+pdhg_status batch_persistent_solve(pdhg_ctx* ctx, long long k0, long long max_iter);
 
 }  // namespace pdhg

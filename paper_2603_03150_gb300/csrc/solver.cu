@@ -597,6 +597,9 @@ extern "C" void pdhg_default_options(pdhg_options* o) {
   o->pid_kp = 0.99;
   o->pid_ki = 0.01;
   o->pid_kd = 0.0;
+  o->persistent = 0;
+  o->wait_limit_ms = 1000;
+  o->wait_test = 0;
 }
 
 // device attributes, stream, kernel shared-memory limits

@@ -61,6 +61,9 @@ class Options(ctypes.Structure):
         ("pid_kp", ctypes.c_double),
         ("pid_ki", ctypes.c_double),
         ("pid_kd", ctypes.c_double),
+        ("persistent", ctypes.c_int32),
+        ("wait_limit_ms", ctypes.c_int32),
+        ("wait_test", ctypes.c_int32),
     ]
 
 

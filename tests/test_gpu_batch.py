@@ -128,3 +128,65 @@ def test_batch_invalid_local_column_rejected():
     with pytest.raises(pdhg.PDHGError) as e:
         pdhg.BatchSolver(lps)
     assert e.value.status == pdhg.PDHG_INVALID_ARG
+
+
+# ---------------------------------------------------------------- persistent launch
+def test_persistent_batch_equals_the_graph_path():
+    """One cooperative launch for the whole batched solve (options.persistent)
+    runs the same kernels in the same order as the graph of per-half-step
+    launches on the same schedules (8 nonzeros per thread, full tiles): the
+    float64 solves agree bit for bit, LP by LP."""
+    lps = lpgen.planted_batch(count=16, m_lo=50, m_hi=600)
+    out = {}
+    for persistent in (0, 1):
+        with pdhg.BatchSolver(lps, persistent=persistent, tile_nnz=2044) as s:
+            assert s.solve(1e-4, 200_000) == pdhg.PDHG_CONVERGED
+            g = s.get()
+            out[persistent] = (np.asarray(g["x"]).copy(), np.asarray(g["y"]).copy(), g["iters"].copy())
+    assert np.array_equal(out[0][2], out[1][2])
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_persistent_batch_iterates_match_oracle():
+    lps = lpgen.planted_batch(count=8, m_lo=50, m_hi=400)
+    with pdhg.BatchSolver(lps, persistent=1) as s:
+        s.solve(1e-4, 100_000)
+        g = s.get()
+    xs = s.split(g["x"], "n")
+    for i, lp in enumerate(lps):
+        r = O.solve(lp, 1e-4, 100_000)
+        assert g["iters"][i] == r.iters
+        assert rel_inf(xs[i], r.x) < 1e-8
+
+
+def test_persistent_fp32_batch_meets_the_test_in_fp64():
+    lps = lpgen.planted_batch(count=12, m_lo=50, m_hi=600)
+    with pdhg.BatchSolver(lps, precision="fp32", persistent=1) as s:
+        assert s.solve(1e-4, 200_000) == pdhg.PDHG_CONVERGED
+        g = s.get()
+        checks, rejects = s.fp64_checks()
+    assert checks - rejects == len(lps)
+    xs, ys = s.split(g["x"], "n"), s.split(g["y"], "m")
+    for i, lp in enumerate(lps):
+        A = O.as_csr(lp.m, lp.n, lp.row_ptr, lp.col, lp.val)
+        ok, rp, rd, gap = O.termination_test(A, lp.b, lp.c, xs[i], ys[i], 1e-4)
+        assert ok, (i, rp, rd, gap)
+
+
+def test_persistent_barrier_wait_runs_out_to_timeout():
+    """A grid barrier that waits for an arrival nothing makes (options.wait_test)
+    gives up after wait_limit_ms: every block returns, the solve reports
+    PDHG_TIMEOUT, and the GPU goes on working (a fresh batch then solves)."""
+    import time
+    lps = lpgen.planted_batch(count=4, m_lo=50, m_hi=200)
+    with pdhg.BatchSolver(lps, persistent=1, wait_test=1, wait_limit_ms=50) as s:
+        t0 = time.perf_counter()
+        st = s.solve(1e-4, 10_000)
+        dt = time.perf_counter() - t0
+        msg = pdhg.lib().pdhg_last_error().decode()
+    assert st == pdhg.PDHG_TIMEOUT
+    assert np.all(s.lp_status == pdhg.PDHG_TIMEOUT)
+    assert 0.04 <= dt < 30.0, dt
+    assert "grid barrier" in msg
+    with pdhg.BatchSolver(lps, persistent=1) as s2:
+        assert s2.solve(1e-4, 100_000) == pdhg.PDHG_CONVERGED
