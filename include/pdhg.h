@@ -132,11 +132,16 @@ typedef struct pdhg_options {
                               grid-wide barriers whose waits are bounded; it
                               runs the SpMV schedules of 8 nonzeros per thread
                               (full tiles) whatever the tuner picked           */
-  int32_t wait_limit_ms;   /* bound of one grid-barrier wait (default 1000); a
-                              wait past it ends the solve with PDHG_TIMEOUT   */
+  int32_t wait_limit_ms;   /* bound of one device-side wait (default 1000): a
+                              grid barrier of the persistent batched solve,
+                              or the bulk copy of a column panel of the
+                              gathered vector; a wait past it ends the solve
+                              with PDHG_TIMEOUT                               */
   int32_t wait_test;       /* 1: every grid barrier waits for one arrival more
-                              than the grid has, so the bounded wait runs out
-                              (tests the PDHG_TIMEOUT path; default 0)        */
+                              than the grid has, and every column-panel load
+                              for 16 bytes more than its copies deliver, so
+                              the bounded waits run out (tests the
+                              PDHG_TIMEOUT path; default 0)                   */
 } pdhg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -165,7 +170,10 @@ pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const int32_t* row
  * converges when the screened iterate passes the test in float64 (x~, y~
  * widened to float64, A~x~ and A~^T y~ recomputed from the float64 scaled
  * matrices), so a converged float32-mixed solve meets the test at eps_rel
- * exactly as pdhg_get reports it.  */
+ * exactly as pdhg_get reports it.  If a column-panel SpMV's bounded wait for
+ * its bulk copy ran out (options.wait_limit_ms), the call returns
+ * PDHG_TIMEOUT and pdhg_last_error says so; the iterate is then not
+ * meaningful, the context stays usable.  */
 pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_iter);
 
 /* The returned iterate (the one that passed the test, else the current one)

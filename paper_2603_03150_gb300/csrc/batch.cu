@@ -907,12 +907,6 @@ struct PersistArgs {
   const int32_t *lp_t8, *lp_a8;
 };
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // false in every thread of the block once any block's wait ran past limit_ns
 __device__ __forceinline__ bool grid_barrier(GridSync* g, unsigned long long limit_ns) {
   __shared__ int ok;

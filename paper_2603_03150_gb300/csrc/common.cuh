@@ -83,6 +83,9 @@ struct PanelView {
   int32_t P, npanels, rows, cols, nblocks, ntiles;
   int32_t pscap;        // pseudo-rows of a tile at most (128 or 256): the staged sums per warp
   int32_t pstride;      // rows rounded up to a multiple of 4 (16-byte aligned panels)
+  int32_t* err;         // set to 1 when the panel load's bounded wait ran out
+  uint32_t tx_extra;    // bytes the load expects beyond its copies (16 to test the bound, else 0)
+  unsigned long long wait_ns;  // bound of the panel load's wait
 };
 
 // ---------------------------------------------------------------------------
@@ -262,6 +265,49 @@ __device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes) {
 // Launched without the attribute both are no-ops.
 __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Wall-clock time of the GPU in ns (bounds of device-side waits).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A shared-memory transaction barrier (mbarrier) for bulk copies into shared
+// memory: one arrival (the thread that issues the copies) plus the bytes the
+// copies deliver.  mb is the barrier's shared-memory address.
+__device__ __forceinline__ void mbar_init(uint32_t mb) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t mb, uint32_t bytes) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(mb),
+               "r"(bytes)
+               : "memory");
+}
+// global [src, src + bytes) -> shared dst (both 16-byte aligned, bytes a
+// multiple of 16), completing on the barrier mb
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                              uint32_t mb) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mb)
+      : "memory");
+}
+// waits for phase `parity` of the barrier to complete, at most limit_ns
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
 }
 
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }

@@ -140,6 +140,7 @@ struct pdhg_ctx {
   DevSched sa, st;      // iteration schedules (autotuned nonzeros per thread)
   DevSched sa8, st8;    // float64 report / Algorithm 1 / power iteration
   DevPanel pa, pt;      // column panels of A~ (dual) and A~^T (primal), when chosen
+  int32_t* panel_err = nullptr;  // 1 once a panel load's bounded wait ran out
   int panel_row_grid_a = 1, panel_row_grid_t = 1;
   Launch l_prim{}, l_dual{}, l_eval{}, l_a64{}, l_t64{};
   int restart_grid = 1;

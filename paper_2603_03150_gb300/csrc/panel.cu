@@ -69,6 +69,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   float* stage = smem;               // [warps][pscap] pseudo-row sums
   PanelTile* dc = reinterpret_cast<PanelTile*>(smem + stage_len);  // the first tiles of the block
   int* next_tile = reinterpret_cast<int*>(smem + stage_len + 4 * kPanelDescCache);
+  // the panel load's transaction barrier, in static shared memory: placed in
+  // the dynamic region beside the tile counter and the panel, the same
+  // kernel took about 1 us longer per launch on the power-law LP
+  __shared__ __align__(8) unsigned long long panel_bar;
+  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&panel_bar);
   float* vs = smem + stage_len + 4 * kPanelDescCache + 4;           // the panel of v
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const PanelBlock bd = V.blocks[blockIdx.x];
@@ -113,7 +118,10 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     dc[q] = V.tiles[bd.t_begin + q];
   // the first tile of each warp is fixed; the others go to whichever warp
   // finishes first (tile sizes and long pseudo-rows vary)
-  if (tid == 0) *next_tile = bd.t_begin + kPanelWarps;
+  if (tid == 0) {
+    *next_tile = bd.t_begin + kPanelWarps;
+    mbar_init(mb);
+  }
   __syncthreads();
   int t = bd.t_begin + warp;
   PanelLoad cur;  // the first tile's loads go out before the wait
@@ -121,25 +129,31 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   pdl_enter();
   if (sc->done) return;
   {
-    // the panel of v: 6 loads in flight per thread before their stores
-    constexpr int U = 6;
+    // the panel of v: whole 16-byte pieces by the bulk-copy engine (one
+    // thread issues 32 KB copies onto the transaction barrier), the tail by
+    // the threads.  The panel starts 32-byte aligned (P is a multiple of 8)
+    // and so does its place in shared memory.  The wait is bounded
+    // (options.wait_limit_ms): past it the block flags the error, waits once
+    // more for its copies in flight, and returns without its work (the solve
+    // reports a timeout).
     const int c0 = bd.panel * V.P;
     const int cnt = min(V.P, V.cols - c0);
-    const float4* src = reinterpret_cast<const float4*>(v + c0);
-    float4* dst = reinterpret_cast<float4*>(vs);
-    const int n4 = cnt >> 2;
-    for (int q0 = tid; q0 < n4; q0 += U * kPanelThreads) {
-      float4 tmp[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (q0 + u * kPanelThreads < n4) tmp[u] = __ldg(src + q0 + u * kPanelThreads);
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (q0 + u * kPanelThreads < n4) dst[q0 + u * kPanelThreads] = tmp[u];
+    const uint32_t bytes = ((uint32_t)cnt * 4u) & ~15u;
+    if (tid == 0) {
+      mbar_arrive_expect(mb, bytes + V.tx_extra);
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(vs);
+      const char* src = reinterpret_cast<const char*>(v + c0);
+      constexpr uint32_t kPiece = 32768;
+      for (uint32_t o = 0; o < bytes; o += kPiece) bulk_copy_g2s(dst + o, src + o, min(kPiece, bytes - o), mb);
     }
-    for (int q = (n4 << 2) + tid; q < cnt; q += kPanelThreads) vs[q] = __ldg(v + c0 + q);
+    for (int q = (int)(bytes >> 2) + tid; q < cnt; q += kPanelThreads) vs[q] = __ldg(v + c0 + q);
+    const bool ok = mbar_wait(mb, 0, V.wait_ns);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(V.err, 1);
+      mbar_wait(mb, 0, V.wait_ns);
+      return;
+    }
   }
-  __syncthreads();
   float* st = stage + warp * V.pscap;
   float* part = V.partial + (size_t)bd.panel * V.pstride;
   while (t < bd.t_end) {
@@ -445,6 +459,16 @@ size_t panel_smem(int P, int pscap) {
          ((size_t)kPanelWarps * pscap + 4 * (size_t)kPanelDescCache + 4 + (size_t)P);
 }
 
+// static shared memory of k_panel_spmv (its transaction barrier): the panel
+// width leaves room for it below the opt-in limit
+static size_t panel_static_smem() {
+  static size_t bytes = [] {
+    cudaFuncAttributes fa{};
+    return cudaFuncGetAttributes(&fa, k_panel_spmv) == cudaSuccess ? fa.sharedSizeBytes : size_t(64);
+  }();
+  return bytes;
+}
+
 void launch_panel_half(const IterBuffers<float>& B, const PanelView& V, bool dual, int method,
                        int row_grid, int i, cudaStream_t s, cudaEvent_t between) {
   const float* v = dual ? (method == 1 ? B.x_avg : B.x) : B.y;
@@ -673,7 +697,8 @@ bool panel_shape(const pdhg_ctx* ctx, bool on_a, int* P_out, int* np_out, int ps
   if (!ctx->mixed || ctx->batch || ctx->nnz < 1) return false;
   const int64_t R = on_a ? ctx->m : ctx->n, C = on_a ? ctx->n : ctx->m;
   if (R < 1 || C < 1 || ctx->nnz > (int64_t(1) << 30)) return false;
-  int64_t pmax = ((int64_t)ctx->smem_optin / (int64_t)sizeof(float) - (int64_t)kPanelWarps * pscap -
+  const int64_t dyn = (int64_t)ctx->smem_optin - (int64_t)panel_static_smem();
+  int64_t pmax = (dyn / (int64_t)sizeof(float) - (int64_t)kPanelWarps * pscap -
                   4 * kPanelDescCache - 4) &
                  ~int64_t(7);
   pmax = std::min<int64_t>(pmax, 65536);
@@ -892,6 +917,14 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   V.ntiles = nt;
   V.pscap = pscap;
   V.pstride = pstride;
+  if (!ctx->panel_err) {
+    CKS(dalloc(ctx, &ctx->panel_err, 1));
+    PL_CK(cudaMemsetAsync(ctx->panel_err, 0, sizeof(int32_t), s));
+    PL_CK(cudaStreamSynchronize(s));
+  }
+  V.err = ctx->panel_err;
+  V.tx_extra = ctx->opt.wait_test ? 16u : 0u;
+  V.wait_ns = (unsigned long long)ctx->opt.wait_limit_ms * 1000000ull;
   out->pseudo_rows = nps;
   out->nnz_padded = nzp;
   out->on = nb > 0;

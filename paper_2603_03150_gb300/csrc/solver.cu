@@ -964,10 +964,12 @@ extern "C" pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const i
       !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6) ||
       (ctx->opt.omega_rule != 0 && ctx->opt.omega_rule != 1) ||
       !std::isfinite(ctx->opt.pid_kp) || !std::isfinite(ctx->opt.pid_ki) ||
-      !std::isfinite(ctx->opt.pid_kd)) {
+      !std::isfinite(ctx->opt.pid_kd) || ctx->opt.wait_limit_ms < 1 ||
+      (ctx->opt.wait_test != 0 && ctx->opt.wait_test != 1)) {
     set_error("invalid options (eval_freq >= 1, ruiz_iters >= 0, precision 0/1, "
               "-8 <= tile_nnz <= 8192, method 0/1, 0 <= reflection <= 1, spmv_layout 0..2, "
-              "panel_width >= 0, 1 <= fp32_screen <= 1e6, omega_rule 0/1, finite PID gains)");
+              "panel_width >= 0, 1 <= fp32_screen <= 1e6, omega_rule 0/1, finite PID gains, "
+              "wait_limit_ms >= 1, wait_test 0/1)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }
@@ -1102,6 +1104,16 @@ extern "C" pdhg_status pdhg_solve(pdhg_ctx* ctx, double eps_rel, int64_t max_ite
   CK(cudaMemcpy(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost));
   ctx->last_status = hs.done ? hs.status : PDHG_MAX_ITER;
   if (!hs.done && hs.k >= max_iter) ctx->last_status = PDHG_MAX_ITER;
+  if (ctx->panel_err) {
+    int32_t perr = 0;
+    CK(cudaMemcpy(&perr, ctx->panel_err, sizeof(perr), cudaMemcpyDeviceToHost));
+    if (perr) {
+      CK(cudaMemset(ctx->panel_err, 0, sizeof(int32_t)));
+      set_error("a column-panel load waited longer than options.wait_limit_ms for its bulk "
+                "copy; the iterate is not meaningful");
+      ctx->last_status = PDHG_TIMEOUT;
+    }
+  }
   return (pdhg_status)ctx->last_status;
 }
 

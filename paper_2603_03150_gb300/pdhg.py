@@ -189,7 +189,8 @@ class Solver:
                  kernel_timing: bool = False, method: str = "averaged",
                  reflection: float = 1.0, spmv_layout: str = "auto", panel_width: int = 0,
                  fp32_screen: float = 1.0, omega_rule: str = "smooth", pid_kp: float = 0.99,
-                 pid_ki: float = 0.01, pid_kd: float = 0.0, verbose: bool = False):
+                 pid_ki: float = 0.01, pid_kd: float = 0.0, wait_limit_ms: int = 1000,
+                 wait_test: bool = False, verbose: bool = False):
         L = lib()
         o = Options()
         L.pdhg_default_options(ctypes.byref(o))
@@ -220,6 +221,8 @@ class Solver:
             raise ValueError("omega_rule must be 'smooth' or 'pid'")
         o.omega_rule = 1 if omega_rule == "pid" else 0
         o.pid_kp, o.pid_ki, o.pid_kd = pid_kp, pid_ki, pid_kd
+        o.wait_limit_ms = wait_limit_ms
+        o.wait_test = 1 if wait_test else 0
         o.verbose = 1 if verbose else 0
         self.m, self.n = int(m), int(n)
         self.device_io = device_io

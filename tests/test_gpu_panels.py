@@ -315,3 +315,32 @@ def test_time_kernels_times_real_work_and_leaves_the_state(layout):
         ms3b = s3.time_kernels(20)
         assert s3.info(violation=False)["status"] == pdhg.PDHG_CONVERGED
     assert ms3["dual_ms"] > 0 and ms3b["dual_ms"] > 0
+
+
+def test_panel_load_wait_runs_out_to_timeout():
+    """options.wait_test makes every panel load expect 16 bytes more than its
+    bulk copies deliver, so its transaction barrier never completes: each
+    block gives up after wait_limit_ms, flags the error and returns.  The
+    solve reports PDHG_TIMEOUT with the reason, and the GPU goes on working
+    (a context without the test bytes then solves)."""
+    import time
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    with pdhg.Solver.from_lp(lp, precision="fp32", spmv_layout="panels", wait_test=True,
+                             wait_limit_ms=2, eval_freq=8) as s:
+        t0 = time.perf_counter()
+        st = s.solve(1e-4, 8)
+        dt = time.perf_counter() - t0
+        msg = pdhg.lib().pdhg_last_error().decode()
+    assert st == pdhg.PDHG_TIMEOUT
+    assert "column-panel" in msg
+    # 8 iterations x 2 half-steps, each block waiting twice for 2 ms
+    assert 0.03 <= dt < 30.0, dt
+    with pdhg.Solver.from_lp(lp, precision="fp32", spmv_layout="panels") as s2:
+        assert s2.solve(1e-4, 200_000) == pdhg.PDHG_CONVERGED
+
+
+def test_wait_options_are_validated():
+    lp = lpgen.planted_lp(20, 50, seed=0)
+    for limit in (0, -5):
+        with pytest.raises(pdhg.PDHGError):
+            pdhg.Solver.from_lp(lp, precision="fp32", wait_limit_ms=limit)
