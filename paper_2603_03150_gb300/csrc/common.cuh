@@ -267,6 +267,16 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Lets the next kernel of the stream (launched with programmatic stream
+// serialization) start its blocks as SMs free up, ahead of this grid's end.
+// Its griddepcontrol.wait still waits for this whole grid to complete and
+// flush, so only its prologue over constant data overlaps this kernel.  Every
+// block of this grid calls it, so the next grid starts only after this one's
+// last block is running (no block of this grid waits for an SM).
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Wall-clock time of the GPU in ns (bounds of device-side waits).
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
