@@ -13,8 +13,9 @@
 //   bit  16     the window's first nonzero continues a pseudo-row begun before
 //   bits 17..   pseudo-row of the window's first nonzero, relative to the tile
 // per pseudo-row its row.  A warp owns a tile: lane l holds nonzeros
-// [8l, 8l+8), walks its row ends with one fused multiply-add per nonzero, and
-// a segmented shuffle scan joins pseudo-rows that cross lanes.  No block
+// [8l, 8l+8), walks its row ends with one fused multiply-add per nonzero and a
+// store at each row end, and a segmented shuffle scan joins pseudo-rows that
+// cross lanes.  No block
 // barrier follows the panel load, so 32 warps per SM run independently.
 #include <algorithm>
 #include <cstdio>
@@ -187,16 +188,16 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
           if (k < nps) rid[j] = ld_stream(V.psrow + tl.ps_begin + k, pol);
         }
       }
-      // walk without branches: the running sum is stored at every nonzero
-      // (the last store of a pseudo-row is its sum; a sum still open at the
-      // window's end is replaced below), a row end resets it
+      // walk: a pseudo-row's sum is stored at its last nonzero (a predicated
+      // store), a row end resets the running sum.  A pseudo-row begun in an
+      // earlier lane and ended here (the head) gets the earlier lanes' part
+      // below; one still open at the window's end goes to the scan
       const uint32_t d = cur.d;
-      // lanes past the tile's end hold no nonzeros: no stores, no open sum
+      // lanes past the tile's end hold no nonzeros (d = 0: no row ends)
       const bool active = lane * 8 < tl.nz_len;
-      int r = (int)(d >> 17);
-      bool head = ((d >> 16) & 1u) != 0u;
-      int head_row = -1;
-      float acc = 0.f, head_val = 0.f;
+      const int r0 = (int)(d >> 17);
+      int r = r0;
+      float acc = 0.f;
       {
         float g[8], a[8];
 #pragma unroll
@@ -209,18 +210,15 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           acc = fmaf(a[e], g[e], acc);
-          if (active) st[r] = acc;
-          const bool end = ((d >> e) & 1u) != 0u;
-          const bool close_head = head && end;
-          head_val = close_head ? acc : head_val;
-          head_row = close_head ? r : head_row;
-          head = head && !end;
-          acc = end ? 0.f : acc;
-          r += end ? 1 : 0;
+          if ((d >> e) & 1u) {
+            st[r] = acc;
+            acc = 0.f;
+            ++r;
+          }
         }
       }
       const int key = (active && !((d >> 7) & 1u)) ? r : -1;  // pseudo-row open at the window's end
-      if (!active) head_row = -1;
+      const int head_row = (active && ((d >> 16) & 1u) && (d & 0xffu)) ? r0 : -1;
       // the tile's values, columns and gathers are dead: the next tile's loads
       // go out now and overlap the scan, the head fix-up and the staged writes
       {
@@ -242,6 +240,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       const float cprev = __shfl_up_sync(0xffffffffu, sv, 1);
       __syncwarp();
       if (head_row >= 0) {
+        float head_val = st[head_row];  // this lane's part, stored at the row's end
         if (lane > 0 && kprev == head_row) head_val += cprev;
         st[head_row] = head_val;
       }
