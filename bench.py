@@ -248,7 +248,8 @@ def run_ours(args):
             ev[0].record(stream)
             s = pdhg.Solver(m, n, src["row_ptr"], src["col"], src["val"], src["b"], src["c"],
                             precision=precision, device_io=device_io, stream=stream.cuda_stream,
-                            method=args.method, spmv_layout=args.layout)
+                            method=args.method, spmv_layout=args.layout,
+                            omega_rule=args.omega_rule)
             ev[1].record(stream)
             st = s.solve(EPS, args.max_iter)
             ev[2].record(stream)
@@ -323,7 +324,7 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         sk = pdhg.Solver(m, n, devt["row_ptr"], devt["col"], devt["val"], devt["b"], devt["c"],
                          precision=args.precision, device_io=True, stream=stream.cuda_stream,
-                         method=args.method, spmv_layout=args.layout)
+                         method=args.method, spmv_layout=args.layout, omega_rule=args.omega_rule)
         sk.solve(EPS, args.max_iter)
         kt = sk.time_kernels(args.kernel_reps)
         gf = {"dual": sk.gather_floor(True, 20), "primal": sk.gather_floor(False, 20)}
@@ -379,7 +380,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(lp, args.cpu_iters, args.method)
+        cpu = cpu_baseline(lp, args.cpu_iters, args.method, args.omega_rule)
 
     if rank == 0:
         ms_step = total_ms / max(len(rec), 1)
@@ -390,7 +391,8 @@ def run_ours(args):
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "precision": args.precision +
                        ("_mixed (f64 norms, gap, restart rule, step/weight updates)" if args.precision == "fp32" else ""),
-                       "eps_rel": EPS, "method": args.method, "layout": args.layout,
+                       "eps_rel": EPS, "method": args.method, "omega_rule": args.omega_rule,
+                       "layout": args.layout,
                        "step": "create + solve to eps + get + warmstart_point (create and "
                                "solve also reported apart)",
                        "l2": "flushed between steps (512 MiB write), inputs resident in HBM",
@@ -621,7 +623,7 @@ def run_sweep(args):
                     s = pdhg.Solver(lp.m, lp.n, devt["row_ptr"], devt["col"], devt["val"],
                                     devt["b"], devt["c"], precision=prec, device_io=True,
                                     stream=stream.cuda_stream, method=args.method,
-                                    spmv_layout=args.layout)
+                                    spmv_layout=args.layout, omega_rule=args.omega_rule)
                     st = s.solve(eps, args.max_iter)
                     s.get()
                     e1.record(stream)
@@ -647,7 +649,8 @@ def run_sweep(args):
             "value": value, "unit": f"s ({head.upper()}, eps_rel = 1e-8)", "n_gpus": 1,
             "steps": args.steps, "warmup": 1, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "method": args.method, "layout": args.layout,
+            "config": {"workload": WORKLOADS[args.workload], "method": args.method,
+                       "omega_rule": args.omega_rule, "layout": args.layout,
                        "step": "create + solve to eps + get", "max_iter": args.max_iter,
                        "l2": "flushed between solves (512 MiB write)"},
             "sweep": out, "gpu_launches": launches, "clocks": clk.summary()}
@@ -750,14 +753,14 @@ def run_profile(args):
                           "schedule": s.schedule(), "launches": s.launch_count()}), flush=True)
 
 
-def cpu_baseline(lp, iters, method="averaged"):
+def cpu_baseline(lp, iters, method="averaged", omega_rule="smooth"):
     """The oracle as it stands, timed on this host: its set-up once (timed
     apart), then `iters` PDHG iterations (steady-state iterations per second)."""
     from oracle import pdhg_oracle as O
     t0 = time.perf_counter()
     S = O.setup(lp)
     t1 = time.perf_counter()
-    O.solve(lp, EPS, iters, opts=O.Options(method=method), S=S)
+    O.solve(lp, EPS, iters, opts=O.Options(method=method, omega_rule=omega_rule), S=S)
     t2 = time.perf_counter()
     return {"value": round(iters / (t2 - t1), 3), "unit": "iter/s", "cores": 1, "kind": "oracle",
             "sample": f"{iters} iterations of the float64 numpy/scipy oracle on the same LP after "
@@ -782,7 +785,8 @@ def run_reference(args):
     for i in range(args.warmup + args.steps):
         t = time.perf_counter()
         k += args.ref_iters
-        r = O.solve(lp, EPS, k, opts=O.Options(method=args.method), S=S, state=st)
+        r = O.solve(lp, EPS, k, opts=O.Options(method=args.method, omega_rule=args.omega_rule), S=S,
+                    state=st)
         st = r.state
         zs = np.maximum(0.0, S.c_t - S.At.T @ st.y)
         O.centered_start_point(st.x, zs)
@@ -820,6 +824,8 @@ def main():
                     help="FP32 half-step layout: autotuned (default), CSR tiles or column panels")
     ap.add_argument("--method", choices=["averaged", "halpern"], default="averaged",
                     help="PDHG iteration: restarted averaged (default) or reflected Halpern")
+    ap.add_argument("--omega-rule", choices=["smooth", "pid"], default="smooth",
+                    help="primal weight at restarts: smoothed ratio (default) or PID control")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=128)
     ap.add_argument("--kernel-reps", type=int, default=50,
