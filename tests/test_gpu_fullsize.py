@@ -7,12 +7,21 @@ the float64 oracle:
     the termination test at k = 100) the iterates, running averages and
     primal weight equal the oracle's to 1e-9 relative (infinity norm) and the
     restart log is the oracle's;
+  * float64 to eps_rel = 1e-4: the oracle's own full solve of the same LP
+    (stored in tests/golden/powerlaw_solve_1e-4.json by
+    tests/golden/make_powerlaw_solve_golden.py, several minutes on one core)
+    -- the same iteration and restart counts, the same returned iterate
+    (current or average), residuals, gap, objective and maximum violation
+    within 1e-9 relative;
   * float32-mixed: a solve to eps_rel = 1e-4 meets the Section 2 test at
     1e-4 when the oracle re-evaluates the returned point in float64 (the
     library confirms every screened candidate in float64 before it stops),
     its objective is within 1e-3 relative of the planted optimum, and the
     Section 4.3 maximum violation the library reports equals the oracle's.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -56,6 +65,22 @@ def test_fullsize_fp64_iterates_after_100_match_oracle(c1, oracle_100):
     for e, o in zip(lg, r.log):
         assert abs(e["kkt_cur"] - o["kkt_cur"]) <= 1e-9 * o["kkt_cur"]
         assert abs(e["kkt_avg"] - o["kkt_avg"]) <= 1e-9 * o["kkt_avg"]
+
+
+def test_fullsize_fp64_solve_matches_the_oracle_solve(c1):
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "powerlaw_solve_1e-4.json")))
+    with pdhg.Solver.from_lp(c1) as s:
+        assert s.solve(g["eps_rel"], 2_000_000) == pdhg.PDHG_CONVERGED == g["status"]
+        info = s.info()
+        r = s.get()
+    assert info["iters"] == g["iters"] and info["restarts"] == g["restarts"]
+    assert info["chosen_average"] == (g["chosen"] == "average")
+    for key in ("r_P", "r_D", "gap"):
+        assert abs(r[key] - g[key]) <= 1e-9 * (1 + abs(g[key])), key
+    obj = float(c1.c @ r["x"])
+    assert abs(obj - g["objective"]) <= 1e-9 * (1 + abs(g["objective"]))
+    assert abs(info["max_violation"] - g["max_violation"]) <= 1e-9 * (1 + g["max_violation"])
 
 
 def test_fullsize_fp32_mixed_solve_meets_the_test_in_fp64(c1):
