@@ -231,7 +231,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def run_steps(precision, k, w, device_io=True):
+    def run_steps(precision, k, w, device_io=True, method=None, omega_rule=None):
         """k timed steps after w untimed ones; each step's GPU timeline split
         by events on the solver's stream: create | solve | get + Algorithm 1."""
         outs = None
@@ -248,8 +248,8 @@ def run_ours(args):
             ev[0].record(stream)
             s = pdhg.Solver(m, n, src["row_ptr"], src["col"], src["val"], src["b"], src["c"],
                             precision=precision, device_io=device_io, stream=stream.cuda_stream,
-                            method=args.method, spmv_layout=args.layout,
-                            omega_rule=args.omega_rule)
+                            method=method or args.method, spmv_layout=args.layout,
+                            omega_rule=omega_rule or args.omega_rule)
             ev[1].record(stream)
             st = s.solve(EPS, args.max_iter)
             ev[2].record(stream)
@@ -312,6 +312,23 @@ def run_ours(args):
                     (sum(r["solve_ms"] for r in r64) / 1e3),
                     status=[pdhg.STATUS_NAMES.get(r["status"], r["status"]) for r in r64],
                     max_violation=max(r["max_violation"] for r in r64), objective=r64[-1]["obj"])
+
+    # cuPDLP+'s PID primal weight, with the averaged and the Halpern iteration,
+    # on the same workload and precision (not the default: the timed steps
+    # above run the options the parity tests pin)
+    variants = {}
+    if args.variant_steps > 0 and args.method == "averaged" and args.omega_rule == "smooth":
+        for name, meth in (("pid", "averaged"), ("halpern_pid", "halpern")):
+            rv = run_steps(args.precision, args.variant_steps, 1, method=meth, omega_rule="pid")
+            variants[name] = dict(
+                method=meth, omega_rule="pid",
+                time_to_eps_s=float(np.mean([r["ms"] for r in rv]) / 1e3),
+                create_ms=float(np.mean([r["create_ms"] for r in rv])),
+                solve_ms=float(np.mean([r["solve_ms"] for r in rv])),
+                iters=int(np.mean([r["iters"] for r in rv])),
+                iter_per_s=sum(r["iters"] for r in rv) / (sum(r["ms"] for r in rv) / 1e3),
+                status=[pdhg.STATUS_NAMES.get(r["status"], r["status"]) for r in rv],
+                max_violation=max(r["max_violation"] for r in rv), objective=rv[-1]["obj"])
 
     # roofline of the dominant half-step: back-to-back launches of each
     # half-step on a solved iterate of the same LP (pdhg_time_kernels: CUDA
@@ -421,6 +438,15 @@ def run_ours(args):
             line["objective_rel_err_vs_planted"] = abs(rec[-1]["obj"] - obj) / (1 + abs(obj))
             if fp64:
                 fp64["objective_rel_err_vs_planted"] = abs(fp64["objective"] - obj) / (1 + abs(obj))
+        for v in variants.values():
+            if lp.x_star is not None:
+                obj = float(lp.c @ lp.x_star)
+                v["objective_rel_err_vs_planted"] = abs(v["objective"] - obj) / (1 + abs(obj))
+            if fp64:
+                v["objective_rel_err_vs_fp64"] = (abs(v["objective"] - fp64["objective"]) /
+                                                  (1 + abs(fp64["objective"])))
+        if variants:
+            line["variants"] = variants
         if fp64:
             line["fp64"] = fp64
             line["objective_rel_err_vs_fp64"] = (abs(rec[-1]["obj"] - fp64["objective"]) /
@@ -827,6 +853,8 @@ def main():
     ap.add_argument("--omega-rule", choices=["smooth", "pid"], default="smooth",
                     help="primal weight at restarts: smoothed ratio (default) or PID control")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--variant-steps", type=int, default=2,
+                    help="steps of each PID primal-weight variant reported beside the default")
     ap.add_argument("--cpu-iters", type=int, default=128)
     ap.add_argument("--kernel-reps", type=int, default=50,
                     help="back-to-back launches per half-step for the roofline timing")

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <future>
 #include <string>
 #include <vector>
 
@@ -105,6 +106,10 @@ struct pdhg_ctx {
   double *a_val_orig = nullptr, *t_val_orig = nullptr, *a_val64 = nullptr, *t_val64 = nullptr;
   float *a_val32 = nullptr, *t_val32 = nullptr;
   std::vector<int32_t> h_a_rp, h_t_rp;
+  // [A, A^T][E = 16, 32]: the tuner's other whole-row schedules, built on a
+  // host thread while the GPU runs the power iteration (declared after the
+  // row pointers they read, so an early destruction joins them first)
+  std::future<pdhg::HostSched> presched[2][2];
   // vectors
   double *b = nullptr, *c = nullptr, *b_t64 = nullptr, *c_t64 = nullptr, *D_r = nullptr,
          *D_c = nullptr;

@@ -447,7 +447,10 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
       if (e == kFixedE && cand.second == 0) {
         d = on_a ? ctx->sa8 : ctx->st8;
       } else {
-        HostSched h = build_sched(rp.data(), nrows, e, nullptr, 1, cand.second);
+        std::future<HostSched>& pre = ctx->presched[which][e == 16 ? 0 : 1];
+        HostSched h = (cand.second == 0 && (e == 16 || e == 32) && pre.valid())
+                          ? pre.get()
+                          : build_sched(rp.data(), nrows, e, nullptr, 1, cand.second);
         CKS(upload_sched(ctx, h, &d, on_a ? ctx->a_rp : ctx->t_rp));
       }
       (on_a ? ctx->sa : ctx->st) = d;
@@ -856,6 +859,20 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
   // float64 schedules (the iteration schedules are tuned once the scalars exist)
   CKS(fixed_schedules(ctx));
   stage("float64 schedules");
+
+  // the tuner's E = 16 and E = 32 schedules are host work: build them on a
+  // host thread while the GPU runs the power iteration
+  if (ctx->opt.autotune && ctx->opt.tile_nnz == 0) {
+    for (int which = 0; which < 2; ++which)
+      for (int q = 0; q < 2; ++q) {
+        const int32_t* rp = which == 0 ? ctx->h_a_rp.data() : ctx->h_t_rp.data();
+        const int nrows = which == 0 ? m : n;
+        const int e = q == 0 ? 16 : 32;
+        ctx->presched[which][q] = std::async(std::launch::async, [rp, nrows, e] {
+          return build_sched(rp, nrows, e, nullptr, 1, 0);
+        });
+      }
+  }
 
   // a3: power iteration on A~^T A~ (float64)
   {
