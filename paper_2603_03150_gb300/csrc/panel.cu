@@ -564,17 +564,28 @@ __global__ void k_pl_panel_first(int np, int R, const int32_t* __restrict__ psid
 
 // greedy packing of a segment of one panel's pseudo-rows into warp tiles;
 // emit = false only counts them
+// tile packing: segments of at most kPackSeg pseudo-rows, kPackWarps per block
+constexpr int kPackSeg = 2048, kPackWarps = 4;
+
 template <bool kEmit>
-__global__ void k_pl_pack(int nseg, const int2* __restrict__ segs, const int32_t* __restrict__ seg_panel,
-                          const int32_t* __restrict__ pslen, const int32_t* __restrict__ toff,
-                          int pscap, int32_t* tcount, PanelTile* tiles, int32_t* tlen,
-                          int32_t* tpanel) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nseg) return;
+__global__ void __launch_bounds__(kPackWarps * 32)
+    k_pl_pack(int nseg, const int2* __restrict__ segs, const int32_t* __restrict__ seg_panel,
+              const int32_t* __restrict__ pslen, const int32_t* __restrict__ toff, int pscap,
+              int32_t* tcount, PanelTile* tiles, int32_t* tlen, int32_t* tpanel) {
+  // a warp per segment: its pseudo-row lengths go to shared memory with
+  // coalesced loads, then lane 0 packs them greedily in order
+  __shared__ int32_t sl[kPackWarps][kPackSeg];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kPackWarps + w;
+  if (s >= nseg) return;  // warp-uniform
   const int b = segs[s].x, e = segs[s].y;
+  int32_t* len = sl[w] - b;  // len[k] = pslen[k] for b <= k < e
+  for (int k = b + lane; k < e; k += 32) len[k] = pslen[k];
+  __syncwarp();
+  if (lane != 0) return;
   int nt = 0, k = b;
   while (k < e) {
-    const int L = pslen[k];
+    const int L = len[k];
     PanelTile tl{0, 0, k, 0};
     if (L > kPanelCap) {
       tl.nz_len = (L + 7) & ~7;
@@ -582,9 +593,9 @@ __global__ void k_pl_pack(int nseg, const int2* __restrict__ segs, const int32_t
       ++k;
     } else {
       int used = 0;
-      while (k < e && pslen[k] <= kPanelCap && used + pslen[k] <= kPanelCap &&
+      while (k < e && len[k] <= kPanelCap && used + len[k] <= kPanelCap &&
              k - tl.ps_begin < pscap)
-        used += pslen[k++];
+        used += len[k++];
       tl.nz_len = (used + 7) & ~7;
       tl.nps = k - tl.ps_begin;
     }
@@ -790,8 +801,8 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   k_pl_compact<<<grid_for(len), 256, 0, s>>>(len, R, cnt.p, src.p, psidx.p, out->psrow, pslen.p,
                                              pssrc.p);
 
-  // segments of at most 2048 pseudo-rows within a panel, packed in parallel
-  constexpr int kSeg = 2048;
+  // segments of at most kPackSeg pseudo-rows within a panel, packed in parallel
+  constexpr int kSeg = kPackSeg;
   std::vector<int2> h_segs;
   std::vector<int32_t> h_seg_panel;
   for (int p = 0; p < np; ++p)
@@ -810,7 +821,7 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
     PL_CK(cudaMemcpyAsync(segs.p, h_segs.data(), sizeof(int2) * nseg, cudaMemcpyHostToDevice, s));
     PL_CK(cudaMemcpyAsync(seg_panel.p, h_seg_panel.data(), sizeof(int32_t) * nseg,
                           cudaMemcpyHostToDevice, s));
-    k_pl_pack<false><<<(nseg + 127) / 128, 128, 0, s>>>(nseg, segs.p, seg_panel.p, pslen.p,
+    k_pl_pack<false><<<(nseg + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(nseg, segs.p, seg_panel.p, pslen.p,
                                                          nullptr, pscap, tcount.p, nullptr, nullptr,
                                                          nullptr);
   }
@@ -826,7 +837,7 @@ pdhg_status build_panel_layout(pdhg_ctx* ctx, bool on_a, DevPanel* out) {
   PL_CK(tpanel.alloc(nt));
   PL_CK(nzoff.alloc(nt + 1));
   if (nseg > 0)
-    k_pl_pack<true><<<(nseg + 127) / 128, 128, 0, s>>>(nseg, segs.p, seg_panel.p, pslen.p, toff.p,
+    k_pl_pack<true><<<(nseg + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(nseg, segs.p, seg_panel.p, pslen.p, toff.p,
                                                         pscap, nullptr, out->tiles, tlen.p, tpanel.p);
   launch_scan(tlen.p, nzoff.p, nt, scan_tmp.p, s);
   if (nt > 0) k_pl_tile_begin<<<(nt + 255) / 256, 256, 0, s>>>(nt, nzoff.p, out->tiles);

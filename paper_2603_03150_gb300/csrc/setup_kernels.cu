@@ -262,6 +262,10 @@ __global__ void k_row_stat(int nrows, const int32_t* __restrict__ rp, const int3
                            const double* __restrict__ val, const double* __restrict__ d_self,
                            const double* __restrict__ d_other, int mode, int long_len,
                            double* __restrict__ out) {
+  // mode 0 (Ruiz): the maximum of |a| d over non-negative doubles, taken on
+  // their bit patterns (ordered like the values) with 64-bit integer max, so
+  // only the product and the row's square root use the slow float64 pipe;
+  // mode 1 (Pock-Chambolle): the float64 sum
   constexpr int RPW = 32 / G;  // rows per warp and pass
   const int lane = threadIdx.x & 31, gw = lane / G, gl = lane & (G - 1);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -269,21 +273,27 @@ __global__ void k_row_stat(int nrows, const int32_t* __restrict__ rp, const int3
   for (int base = warp * RPW; base < nrows; base += nw * RPW) {
     const int i = base + gw;
     double acc = 0.0;
+    long long mx = 0;
     bool mine = false;
     if (i < nrows) {
       const int b = rp[i], e = rp[i + 1];
       if (e - b <= long_len) {
         mine = true;
-        for (int k = b + gl; k < e; k += G) {
-          const double a = fabs(val[k]) * d_other[col[k]];
-          acc = mode ? acc + a : fmax(acc, a);
+        if (mode) {
+          for (int k = b + gl; k < e; k += G) acc += fabs(val[k]) * d_other[col[k]];
+        } else {
+          for (int k = b + gl; k < e; k += G)
+            mx = max(mx, __double_as_longlong(fabs(val[k]) * d_other[col[k]]));
         }
       }
     }
+    if (mode) {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      const double t = __shfl_down_sync(0xffffffffu, acc, o, G);
-      acc = mode ? acc + t : fmax(acc, t);
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    } else {
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o, G));
+      acc = __longlong_as_double(mx);
     }
     if (mine && gl == 0) {
       const double r = sqrt(d_self[i] * acc);
@@ -301,14 +311,18 @@ __global__ void k_row_stat_long(const int32_t* __restrict__ ids, const int32_t* 
   __shared__ double red[8];
   const int i = ids[blockIdx.x];
   double acc = 0.0;
-  for (int k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) {
-    const double a = fabs(val[k]) * d_other[col[k]];
-    acc = mode ? acc + a : fmax(acc, a);
-  }
+  long long mx = 0;
+  if (mode) {
+    for (int k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x)
+      acc += fabs(val[k]) * d_other[col[k]];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double t = __shfl_down_sync(0xffffffffu, acc, o);
-    acc = mode ? acc + t : fmax(acc, t);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  } else {
+    for (int k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x)
+      mx = max(mx, __double_as_longlong(fabs(val[k]) * d_other[col[k]]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    acc = __longlong_as_double(mx);
   }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();

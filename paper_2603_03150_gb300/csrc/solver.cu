@@ -709,6 +709,7 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
   void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg, &ctx->Ax_last};
   int32_t* flags = nullptr;
   int32_t *cnt = nullptr, *tmp = nullptr;
+  StageClock sub{ctx};  // verbose: the parts of this stage
   CKS(dalloc(ctx, &flags, 1));
   CKS(dalloc(ctx, &cnt, (size_t)n + 1));
   CKS(dalloc(ctx, &tmp, (size_t)n / 1024 + 8));
@@ -725,6 +726,7 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
               hflags);
     return PDHG_INVALID_ARG;
   }
+  sub("  validation");
 
   // a1: stable transpose A -> A^T (original values)
   CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), ctx->stream));
@@ -758,6 +760,7 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
   }
   CK(cudaGetLastError());
+  sub("  transpose");
 
   // a2: Ruiz (infinity norm) then Pock-Chambolle (alpha = 1)
   RowStatPlan plan_a, plan_t;
@@ -784,6 +787,7 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
     CKS(make_plan(ctx->h_a_rp, m, &plan_a));
     CKS(make_plan(ctx->h_t_rp, n, &plan_t));
   }
+  sub("  row-length plans");
   double *r = ctx->out_m1, *s = ctx->out_n1;
   launch_fill(ctx->D_r, 1.0, m, ctx->stream);
   launch_fill(ctx->D_c, 1.0, n, ctx->stream);
@@ -797,6 +801,7 @@ pdhg_status pdhg::prepare_matrix(pdhg_ctx* ctx) {
     launch_div(ctx->D_r, r, m, ctx->stream);
     launch_div(ctx->D_c, s, n, ctx->stream);
   }
+  sub("  scaling rounds");
   launch_scale_vals(m, ctx->a_rp, ctx->a_col, ctx->a_val_orig, ctx->D_r, ctx->D_c, 0,
                     ctx->a_val64, ctx->a_val32, ctx->stream);
   launch_scale_vals(n, ctx->t_rp, ctx->t_col, ctx->t_val_orig, ctx->D_r, ctx->D_c, 1,
