@@ -418,6 +418,10 @@ static pdhg_status time_iterations(pdhg_ctx* ctx, float* ms_out) {
   return PDHG_OK;
 }
 
+// mean nonzeros per row from which the tuner also tries 16 and 32 nonzeros
+// per thread
+constexpr int kLongWindowRows = 8;
+
 static pdhg_status tune_schedules(pdhg_ctx* ctx) {
   const bool mx = ctx->mixed;
   for (int which = 0; which < 2; ++which) {
@@ -432,9 +436,11 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
       cands.push_back({longest <= 256 ? (tn <= -8 ? -8 : -4) : 8, 0});
     else if (tn > 0)
       cands.push_back({tn <= 2044 ? 8 : (tn <= 4092 ? 16 : 32), tn});
-    else if (ctx->opt.autotune) {
+    else if (ctx->opt.autotune && (int64_t)rp[nrows] >= (int64_t)kLongWindowRows * nrows) {
       // the vector variants were slower than E = 8 on every measured matrix
-      // since the window words; they stay available through tile_nnz < 0
+      // since the window words; they stay available through tile_nnz < 0.
+      // E = 16 and 32 are tried only where rows average kLongWindowRows
+      // nonzeros or more: on shorter rows E = 8 won every measurement
       cands = {{8, 0}, {16, 0}, {32, 0}};
     } else {
       cands = {{8, 0}};
@@ -490,7 +496,8 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
     // anyway and building the panels costs more create time than it saves)
     const int lay = ctx->opt.spmv_layout;
     int pw = 0, np = 0;
-    const bool auto_panels = lay == 0 && cands.size() > 1 && ctx->nnz >= (int64_t(1) << 20);
+    const bool auto_panels = lay == 0 && ctx->opt.autotune && ctx->opt.tile_nnz == 0 &&
+                             ctx->nnz >= (int64_t(1) << 20);
     if ((lay == 2 || auto_panels) && panel_shape(ctx, on_a, &pw, &np)) {
       DevPanel& dp = on_a ? ctx->pa : ctx->pt;
       CKS(build_panel_layout(ctx, on_a, &dp));
@@ -872,6 +879,7 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
       for (int q = 0; q < 2; ++q) {
         const int32_t* rp = which == 0 ? ctx->h_a_rp.data() : ctx->h_t_rp.data();
         const int nrows = which == 0 ? m : n;
+        if ((int64_t)rp[nrows] < (int64_t)kLongWindowRows * nrows) continue;  // not tried
         const int e = q == 0 ? 16 : 32;
         ctx->presched[which][q] = std::async(std::launch::async, [rp, nrows, e] {
           return build_sched(rp, nrows, e, nullptr, 1, 0);
