@@ -570,48 +570,87 @@ def run_batch(args):
 
 
 def run_adjoint(args):
-    """64 LPs of 2000 x 5000: batched solve + active-set polish + adjoint."""
+    """64 LPs of 2000 x 5000, loss = ||x*(b, c) - t||^2 through torch.autograd
+    (forward: batched solve + active-set polish; backward: the adjoint).
+    value: the device path -- one BatchLP (A's context built once, before the
+    timed steps), b, c, t CUDA tensors, forward + backward per step.
+    e2e: the same step from host arrays through lp_solution with a context
+    per call (A, b, c copied in and x, dL/db, dL/dc copied out every step)."""
     import torch
 
     from oracle import adjoint_ref as R
     from paper_2603_03150_gb300 import build as B
-    from paper_2603_03150_gb300 import lpgen, pdhg
+    from paper_2603_03150_gb300 import lpgen
+    from paper_2603_03150_gb300.autograd import BatchLP, lp_solution
 
     B.build()
     lps, targets = lpgen.adjoint_batch(64, 2000, 5000)
+    st = dict(m=np.array([lp.m for lp in lps], np.int32), n=np.array([lp.n for lp in lps], np.int32),
+              row_ptr=np.concatenate([lp.row_ptr for lp in lps]),
+              col=np.concatenate([lp.col for lp in lps]), val=np.concatenate([lp.val for lp in lps]))
+    b0 = np.concatenate([lp.b for lp in lps])
+    c0 = np.concatenate([lp.c for lp in lps])
     tcat = np.concatenate(targets)
+    dev = torch.device("cuda", 0)
+    bt, ct, tt = (torch.tensor(a, device=dev) for a in (b0, c0, tcat))
+    blp = BatchLP(st, device="cuda")
 
-    def step():
-        s = pdhg.BatchSolver(lps)
-        s.solve(EPS, args.max_iter)
-        p = s.polish()
-        a = s.adjoint(2.0 * (p["x"] - tcat))
-        s.close()
-        return p, a
+    def step(b_src, c_src, t_src, lp):
+        b = b_src.clone().requires_grad_(True)
+        c = c_src.clone().requires_grad_(True)
+        x = lp_solution(b, c, lp, eps_rel=EPS, max_iter=args.max_iter)
+        ((x - t_src) ** 2).sum().backward()
+        return x, b.grad, c.grad
 
-    for _ in range(max(1, args.warmup - 2)):
-        step()
-    ms = []
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        p, a = step()
-        torch.cuda.synchronize()
-        ms.append((time.perf_counter() - t0) * 1e3)
-    ms_step = float(np.mean(ms))
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        ms, out = [], None
+        for _ in range(k):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            ms.append((time.perf_counter() - t0) * 1e3)
+        return float(np.mean(ms)), out
+
+    with Clocks(0) as clk:
+        ms_step, (x, gb, gc) = timed(lambda: step(bt, ct, tt, blp), args.steps, args.warmup)
+    bh, ch, th = (torch.from_numpy(a) for a in (b0, c0, tcat))
+    e2e_ms, (xh, gbh, _) = timed(lambda: step(bh, ch, th, st), max(1, args.steps), 1)
+    blp.close()
     lp = lps[0]
-    Bset = lp.x_star > 0
-    A = lp.dense()
-    gr = R.grad_b(A, Bset, 2.0 * (R.polish(A, lp.b, Bset) - targets[0]))
-    err = float(np.linalg.norm(a["grad_b"][:lp.m] - gr) / np.linalg.norm(gr))
+    xs = x.detach().cpu().numpy()[:lp.n]
+    gr = R.grad_b(lp.dense(), xs > 0, 2.0 * (xs - targets[0]))
+    err = float(np.linalg.norm(gb.cpu().numpy()[:lp.m] - gr) / np.linalg.norm(gr))
+    err_h = float(np.linalg.norm(gbh.numpy()[:lp.m] - gb.cpu().numpy()[:lp.m]) /
+                  np.linalg.norm(gb.cpu().numpy()[:lp.m]))
+    sm, sn, nnz = int(st["m"].sum()), int(st["n"].sum()), int(st["val"].size)
+    h2d = 4 * (sm + len(lps)) + 12 * nnz + 8 * sm + 8 * sn
+    d2h = 8 * sn + 8 * sm + 8 * sn
     line = {"metric": "gradients dL/db, dL/dc per second (64 LPs, batched solve + polish + adjoint)",
             "value": round(64 / (ms_step / 1e3), 2), "unit": "LP-gradients/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOADS["adjoint"], "eps_rel": EPS},
-            "grad_b_rel_err_vs_dense_lp0": err, "active_set_sizes": sorted(set(p["active"].tolist())),
-            "cg_iters_max": int(a["cg_iters"].max())}
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["adjoint"], "eps_rel": EPS,
+                       "step": "autograd forward (solve + polish) and backward (adjoint) on one "
+                               "BatchLP; b, c, x and the gradients CUDA tensors"},
+            "e2e": {"value": round(64 / (e2e_ms / 1e3), 2), "unit": "LP-gradients/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": round(e2e_ms, 2),
+                    "step": "host arrays through lp_solution, a context per call"},
+            "grad_b_rel_err_vs_dense_lp0": err, "grad_b_host_vs_device_rel": err_h,
+            "polished_support_sizes": sorted(set(blp_active_sizes(x, st))),
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
+
+
+def blp_active_sizes(x, st):
+    """Positive entries per LP of a polished x."""
+    xs = x.detach().cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(st["n"])])
+    return [int((xs[off[i]:off[i + 1]] > 0).sum()) for i in range(len(st["n"]))]
 
 
 def run_sweep(args):
