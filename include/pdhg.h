@@ -202,7 +202,7 @@ pdhg_status pdhg_get_info(pdhg_ctx* ctx, int64_t* iters, int64_t* restarts,
                           double* max_violation, int32_t* chosen_average,
                           int32_t* last_status);
 
-/* Algorithm 1, lines 2-11 (Section 3.1), computed on device on the scaled
+/* Algorithm 1's centered start point (Section 3.1), computed on device on the scaled
  * returned iterate (x~, y~, z~ = max(0, c~ - A~^T y~)):
  *   mu = max(x~^T z~ / n, mu_min); per j lift to alpha_min, then move the
  *   smaller of the pair toward mu / (other) within +-delta_max, then the

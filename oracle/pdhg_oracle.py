@@ -22,7 +22,7 @@ The paper (Rothberg, "Hybridizing PDHG and Interior-Point Methods") fixes:
 * that scaling makes row and column norms roughly 1 and is essential for
   PDHG (Sections 2.1 and 3.1);
 * the maximum-violation metric (Section 4.3);
-* Algorithm 1 lines 2-11 with mu_min = alpha_min = 1e-6, delta_max = 1e-4
+* Algorithm 1's centered start point with mu_min = alpha_min = 1e-6, delta_max = 1e-4
   (Section 3.1).
 
 It does NOT give the PDHG update, scaling method, step size, restart rule or
@@ -499,11 +499,11 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
 
 
 # ---------------------------------------------------------------------------
-# a9: Algorithm 1, lines 2-11 (Section 3.1)
+# a9: Algorithm 1's centered start point (Section 3.1)
 # ---------------------------------------------------------------------------
 def centered_start_point(x, z, mu_min: float = 1e-6, delta_max: float = 1e-4,
                          alpha_min: float = 1e-6):
-    """Algorithm 1 ("Centered start point"), lines 2-11.
+    """Algorithm 1 ("Centered start point"): the target mu, then the per-entry update.
 
     mu_target = max(x^T z / n, mu_min) from the unclamped input; each pair is
     lifted to at least alpha_min, then the smaller of (x'_j, z'_j) is moved

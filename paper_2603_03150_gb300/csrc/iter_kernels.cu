@@ -427,7 +427,7 @@ void launch_fp64_check(const IterBuffers<T>& B, const Fp64Check& C, cudaStream_t
 template void launch_fp64_check<float>(const IterBuffers<float>&, const Fp64Check&, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Algorithm 1 (Section 3.1), lines 2-11.
+// Algorithm 1 (Section 3.1): the centered start point (target mu, then the per-entry update).
 // ---------------------------------------------------------------------------
 struct WsEpi {
   const double *x_s, *c_t;

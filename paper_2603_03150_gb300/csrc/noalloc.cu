@@ -55,7 +55,7 @@ __device__ __forceinline__ double na_move(double target, double v, double delta)
   return fmin(fmax(target, v - delta), v + delta);
 }
 
-// Algorithm 1, lines 4-10 (Section 3.1), per entry
+// Algorithm 1's per-entry update (Section 3.1)
 __global__ void k_na_apply(int n, const double* __restrict__ x, const double* __restrict__ z,
                            const double* scratch, double delta, double alpha,
                            double* __restrict__ x_out, double* __restrict__ z_out) {

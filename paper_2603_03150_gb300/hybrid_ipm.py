@@ -3,8 +3,8 @@ interior-point method and the bump loop of Algorithm 1 (Section 3.1).
 
 The paper runs PDHG on the GPU and its interior-point solver on the CPU
 (Section 4.1), warm-started from Algorithm 1's point (x', y, z') and raising
-alpha_min tenfold while the first interior-point step is very small (a step
-of at least 1e-6 worked in its tests).  This module is that CPU stage in its
+alpha_min tenfold for as long as the first interior-point step stays below a
+minimum length (1e-6 in its tests).  This module is that CPU stage in its
 plainest textbook form - Mehrotra's predictor-corrector on the normal
 equations, dense Cholesky - so that the effect of the GPU's start point on
 interior-point iteration counts can be measured (Section 4.6 reports the
@@ -133,7 +133,7 @@ def mehrotra(A, b, c, start=None, tol=1e-8, max_iter=200, step_frac=0.99,
 
 
 def warm_start(A, b, c, x, y, z, alpha_min=1e-6, min_step=1e-6, max_bumps=12, **kw):
-    """Algorithm 1, lines 12-17: start the interior-point method from
+    """Algorithm 1's bump loop: start the interior-point method from
     (x', y, z'); while its first step is shorter than min_step, multiply
     alpha_min by 10 and raise every x'_j, z'_j to at least alpha_min.
     Returns the interior-point result with 'bumps' (how many times alpha_min

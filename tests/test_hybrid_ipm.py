@@ -1,5 +1,5 @@
-"""The host-side interior-point consumer of the warm-start point (Algorithm 1
-lines 12-17, Section 3.1): pinned against HiGHS (scipy.optimize.linprog) and
+"""The host-side interior-point consumer of the warm-start point (Algorithm 1's
+bump loop, Section 3.1): pinned against HiGHS (scipy.optimize.linprog) and
 the Section 2 test; the bump loop's mechanics; warm starts from the oracle's
 PDHG point."""
 import numpy as np
