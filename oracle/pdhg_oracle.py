@@ -94,6 +94,7 @@ class Options:
     pid_kp: float = 0.99
     pid_ki: float = 0.01
     pid_kd: float = 0.0
+    step_rule: str = "constant"  # or "adaptive" (PDLP's adaptive step, see adaptive_step)
 
 
 # ---------------------------------------------------------------------------
@@ -362,6 +363,9 @@ class State:
     kkt_prev: float = 0.0   # KKT error of the previous evaluation's candidate
     pid_integral: float = 0.0  # omega_rule "pid": sum of the errors so far
     pid_prev: float = 0.0      # omega_rule "pid": the previous restart's error
+    eta: float = 0.0           # step_rule "adaptive": the next attempt's step (0: setup's eta)
+    eta_sum: float = 0.0       # step_rule "adaptive": accepted steps since the last restart
+    step_rejects: int = 0      # step_rule "adaptive": rejected attempts so far
 
 
 @dataclass
@@ -392,6 +396,32 @@ def initial_state(S: Setup) -> State:
     st.kkt_last = kkt_error(S.At, S.b_t, S.c_t, st.x, st.y, st.omega)
     st.kkt_prev = st.kkt_last
     return st
+
+
+def adaptive_step(dx, dy, A_dx, eta: float, omega: float, j: int) -> dict:
+    """PDLP's adaptive step size (Applegate et al. 2021, "Practical large-scale
+    linear programming using primal-dual hybrid gradient"), as read here.  An
+    attempt with step eta moved the iterate by (dx, dy), and A_dx = A~ x+ - A~ x.
+    The largest step the move allows is
+        eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy^T A_dx|)
+    (infinite when dy^T A_dx = 0); the attempt is accepted when eta <= eta_max,
+    and the next attempt uses
+        min((1 - (j + 1)^-0.3) eta_max, (1 + (j + 1)^-0.6) eta),
+    j = step attempts so far including this one (so the first factor is
+    positive from the first attempt)."""
+    inter = abs(float(np.dot(dy, A_dx)))
+    num = omega * float(np.dot(dx, dx)) + float(np.dot(dy, dy)) / omega
+    eta_max = num / (2.0 * inter) if inter > 0.0 else float("inf")
+    eta_next = min((1.0 - (j + 1.0) ** -0.3) * eta_max, (1.0 + (j + 1.0) ** -0.6) * eta)
+    return dict(accept=eta <= eta_max, eta_max=eta_max, eta_next=eta_next)
+
+
+def step_weighted_average(avg, x, eta: float, eta_sum_before: float):
+    """Running average weighted by the accepted steps: after accepting x with
+    step eta, avg = (sum of eta_i x_i) / (sum of eta_i) over the accepted
+    iterates since the last restart (eta_sum_before = that sum before x)."""
+    total = eta_sum_before + eta
+    return avg + (x - avg) * (eta / total), total
 
 
 def _unscale(S: Setup, xs, ys):
@@ -428,9 +458,30 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
         raise ValueError("method must be 'averaged' or 'halpern', reflection in [0, 1]")
     if opts.omega_rule not in ("smooth", "pid"):
         raise ValueError("omega_rule must be 'smooth' or 'pid'")
+    adaptive = opts.step_rule == "adaptive"
+    if opts.step_rule not in ("constant", "adaptive") or (adaptive and halpern):
+        raise ValueError("step_rule must be 'constant' or 'adaptive' (averaged method only)")
+    if adaptive and st.eta <= 0.0:
+        st.eta = S.eta  # the first attempt takes the constant step
     while st.k < max_iter:
-        tau, sigma = S.eta / st.omega, S.eta * st.omega
-        if halpern:
+        eta = st.eta if adaptive else S.eta
+        tau, sigma = eta / st.omega, eta * st.omega
+        if adaptive:
+            # one step attempt: accepted (the iterate and the step-weighted
+            # averages move) or rejected (nothing moves); either way the next
+            # attempt's step comes from adaptive_step and k, t count it
+            xn, yn = pdhg_step(At, b_t, c_t, st.x, st.y, tau, sigma)
+            a = adaptive_step(xn - st.x, yn - st.y, At @ xn - At @ st.x, eta, st.omega, st.k + 1)
+            if a["accept"]:
+                st.x, st.y = xn, yn
+                st.x_avg, _ = step_weighted_average(st.x_avg, st.x, eta, st.eta_sum)
+                st.y_avg, st.eta_sum = step_weighted_average(st.y_avg, st.y, eta, st.eta_sum)
+            else:
+                st.step_rejects += 1
+            st.eta = a["eta_next"]
+            st.k += 1
+            st.t += 1
+        elif halpern:
             # z <- lam ((1 + rho) T(z) - rho z) + (1 - lam) z0, z0 = last restart point
             xh, yh = pdhg_step(At, b_t, c_t, st.x, st.y, tau, sigma)
             lam, rho = (st.t + 1.0) / (st.t + 2.0), opts.reflection
@@ -484,6 +535,7 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
             st.x_avg = np.zeros_like(st.x)
             st.y_avg = np.zeros_like(st.y)
             st.t = 0
+            st.eta_sum = 0.0
             st.restarts += 1
             entry.update(dx=dx, dy=dy, omega_new=st.omega, pid_integral=st.pid_integral)
         log.append(entry)

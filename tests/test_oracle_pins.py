@@ -581,3 +581,104 @@ def test_pid_solve_reaches_the_planted_optimum():
     obj = float(lp.c @ lp.x_star)
     assert abs(float(lp.c @ r.x) - obj) <= 1e-5 * (1 + abs(obj))
     assert any("pid_integral" in e for e in r.log)
+
+
+# ----------------------------------------------------- adaptive step (PDLP)
+ADAPT = json.load(open(os.path.join(GOLD, "adaptive_step_cases.json")))
+
+
+def _adapt_case_ok(fn, c):
+    a = fn(np.array(c["dx"]), np.array(c["dy"]), np.array(c["A_dx"]), c["eta"], c["omega"], c["j"])
+    em = float("inf") if c["eta_max"] == "inf" else c["eta_max"]
+    return (a["accept"] == c["accept"] and a["eta_max"] == pytest.approx(em, rel=1e-14)
+            and a["eta_next"] == pytest.approx(c["eta_next"], rel=1e-14))
+
+
+def test_adaptive_step_hand_cases():
+    for c in ADAPT["cases"]:
+        assert _adapt_case_ok(O.adaptive_step, c), c["name"]
+
+
+def _adaptive_slip(kind):
+    def f(dx, dy, A_dx, eta, omega, j):
+        inter = float(np.dot(dy, A_dx)) if kind == "no_abs" else abs(float(np.dot(dy, A_dx)))
+        if kind == "omega_swapped":
+            num = float(np.dot(dx, dx)) / omega + omega * float(np.dot(dy, dy))
+        else:
+            num = omega * float(np.dot(dx, dx)) + float(np.dot(dy, dy)) / omega
+        two = 1.0 if kind == "no_two" else 2.0
+        em = num / (two * inter) if inter != 0.0 else float("inf")
+        jj = j if kind == "j_excludes_current" else j + 1.0
+        p1, p2 = (-0.6, -0.3) if kind == "exponents_swapped" else (-0.3, -0.6)
+        nxt = min((1.0 - jj ** p1) * em, (1.0 + jj ** p2) * eta)
+        return dict(accept=eta <= em, eta_max=em, eta_next=nxt)
+    return f
+
+
+@pytest.mark.parametrize("kind", ["no_abs", "omega_swapped", "no_two", "j_excludes_current",
+                                  "exponents_swapped"])
+def test_adaptive_step_pins_catch_planted_slips(kind):
+    slip = _adaptive_slip(kind)
+    assert not all(_adapt_case_ok(slip, c) for c in ADAPT["cases"]), kind
+
+
+def test_step_weighted_average_by_hand():
+    g = ADAPT["weighted_average"]
+    avg, total = np.zeros(1), 0.0
+    for x, eta, want, s in zip(g["x"], g["eta"], g["averages"], g["sums"]):
+        avg, total = O.step_weighted_average(avg, np.array([x]), eta, total)
+        assert avg[0] == pytest.approx(want, rel=1e-15) and total == s
+
+
+def test_small_steps_are_always_accepted():
+    """|dy^T A dx| <= ||A|| ||dx|| ||dy|| <= ||A|| (omega ||dx||^2 + ||dy||^2 / omega) / 2,
+    so eta_max >= 1 / ||A||_2 for every move: a step at 1 / ||A||_2 is never
+    rejected, while large steps are."""
+    rng = np.random.default_rng(11)
+    rejected = 0
+    for _ in range(200):
+        A = rng.normal(size=(7, 5))
+        dx, dy = rng.normal(size=5), rng.normal(size=7)
+        omega = float(np.exp(rng.uniform(-2, 2)))
+        s = float(np.linalg.norm(A, 2))
+        assert O.adaptive_step(dx, dy, A @ dx, 1.0 / s, omega, 5)["accept"]
+        rejected += not O.adaptive_step(dx, dy, A @ dx, 100.0 / s, omega, 5)["accept"]
+    assert rejected > 0
+
+
+def test_adaptive_rejection_leaves_the_iterate_and_averages():
+    """From the start with a step 100x the constant one: the attempt is
+    rejected (nothing but the step and the counters moves, the step shrinks);
+    attempts go on shrinking it until one is accepted, which moves the
+    iterate, and the accepted step then satisfies eta <= eta_max."""
+    lp = lpgen.planted_lp(200, 500, seed=0)
+    opts = O.Options(step_rule="adaptive")
+    S = O.setup(lp, opts)
+    st = O.initial_state(S)
+    st.eta = 100.0 * S.eta
+    x0, y0, xa0 = st.x.copy(), st.y.copy(), st.x_avg.copy()
+    r = O.solve(lp, 1e-12, 1, opts=opts, S=S, state=st)
+    st = r.state
+    assert st.step_rejects == 1 and st.k == 1 and st.t == 1 and st.eta < 100.0 * S.eta
+    assert np.array_equal(st.x, x0) and np.array_equal(st.y, y0) and np.array_equal(st.x_avg, xa0)
+    assert st.eta_sum == 0.0
+    for k in range(2, 40):
+        eta, rej = st.eta, st.step_rejects
+        st = O.solve(lp, 1e-12, k, opts=opts, S=S, state=st).state
+        if st.step_rejects == rej:  # accepted: the iterate moved with step eta
+            assert not np.array_equal(st.x, x0) and st.eta_sum == eta
+            assert np.array_equal(st.x_avg, st.x)  # the first accepted iterate is the average
+            break
+    else:
+        raise AssertionError("no attempt accepted")
+
+
+def test_adaptive_solve_reaches_the_planted_optimum():
+    for lp in (lpgen.planted_lp(200, 500, seed=0), lpgen.planted_lp(500, 1250, seed=2)):
+        r = O.solve(lp, 1e-6, 100_000, opts=O.Options(step_rule="adaptive"))
+        assert r.status == O.STATUS_CONVERGED
+        obj = float(lp.c @ lp.x_star)
+        assert abs(float(lp.c @ r.x) - obj) <= 1e-5 * (1 + abs(obj))
+    with pytest.raises(ValueError):
+        O.solve(lpgen.planted_lp(20, 50, seed=0), 1e-4, 10,
+                opts=O.Options(step_rule="adaptive", method="halpern"))
