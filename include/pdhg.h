@@ -142,6 +142,17 @@ typedef struct pdhg_options {
                               for 16 bytes more than its copies deliver, so
                               the bounded waits run out (tests the
                               PDHG_TIMEOUT path; default 0)                   */
+  int32_t step_rule;       /* 0 (default): constant step eta = eta_safety /
+                              sigma_max; 1: PDLP's adaptive step (Applegate et
+                              al. 2021): each attempt's move (dx, dy) allows
+                              eta_max = (w||dx||^2 + ||dy||^2/w) /
+                              (2|dy^T A~ dx|), w the primal weight; accepted
+                              when eta <= eta_max, else undone; next step
+                              min((1-(j+1)^-0.3) eta_max, (1+(j+1)^-0.6) eta)
+                              with j the attempts so far; averages weighted
+                              by the accepted steps; attempts count as
+                              iterations.  Single LPs, method 0, CSR tiles
+                              (spmv_layout 2 and batches: PDHG_INVALID_ARG) */
 } pdhg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -187,6 +198,15 @@ pdhg_status pdhg_get(pdhg_ctx* ctx, double* x, double* y, double* z, double* r_P
  * pdhg_get_state / pdhg_set_state.  Single-LP contexts.  */
 pdhg_status pdhg_get_pid_state(pdhg_ctx* ctx, double* integral, double* prev_error);
 pdhg_status pdhg_set_pid_state(pdhg_ctx* ctx, double integral, double prev_error);
+
+/* The adaptive step's state (options.step_rule = 1): the next attempt's step
+ * eta, the sum of the accepted steps since the last restart (the averages'
+ * weight), and the rejected attempts so far (get only); part of a checkpoint
+ * beside pdhg_get_state / pdhg_set_state.  Setting also resets tau, sigma and
+ * the next averaging weight from them.  eta > 0, eta_sum >= 0, finite; else
+ * PDHG_INVALID_ARG.  Single-LP contexts.  */
+pdhg_status pdhg_get_step_state(pdhg_ctx* ctx, double* eta, double* eta_sum, int64_t* rejects);
+pdhg_status pdhg_set_step_state(pdhg_ctx* ctx, double eta, double eta_sum);
 
 /* Float64 checks of float32-mixed candidates in the last solve (single LP
  * or summed over a batch): how many screened candidates were re-evaluated

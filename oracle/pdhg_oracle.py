@@ -401,7 +401,9 @@ def initial_state(S: Setup) -> State:
 def adaptive_step(dx, dy, A_dx, eta: float, omega: float, j: int) -> dict:
     """PDLP's adaptive step size (Applegate et al. 2021, "Practical large-scale
     linear programming using primal-dual hybrid gradient"), as read here.  An
-    attempt with step eta moved the iterate by (dx, dy), and A_dx = A~ x+ - A~ x.
+    attempt with step eta moved the iterate by (dx, dy), and A_dx = A~ dx (A~
+    applied to the move itself: a difference of the products A~ x+ and A~ x
+    would lose the term's leading digits when the move is small).
     The largest step the move allows is
         eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy^T A_dx|)
     (infinite when dy^T A_dx = 0); the attempt is accepted when eta <= eta_max,
@@ -471,7 +473,8 @@ def solve(lp, eps_rel: float = 1e-4, max_iter: int = 100_000,
             # averages move) or rejected (nothing moves); either way the next
             # attempt's step comes from adaptive_step and k, t count it
             xn, yn = pdhg_step(At, b_t, c_t, st.x, st.y, tau, sigma)
-            a = adaptive_step(xn - st.x, yn - st.y, At @ xn - At @ st.x, eta, st.omega, st.k + 1)
+            dx = xn - st.x
+            a = adaptive_step(dx, yn - st.y, At @ dx, eta, st.omega, st.k + 1)
             if a["accept"]:
                 st.x, st.y = xn, yn
                 st.x_avg, _ = step_weighted_average(st.x_avg, st.x, eta, st.eta_sum)

@@ -1396,10 +1396,11 @@ extern "C" pdhg_status pdhg_batch_create(pdhg_ctx** out, int32_t count, const in
       ctx->opt.method != 0 || !(ctx->opt.fp32_screen >= 1.0 && ctx->opt.fp32_screen <= 1e6) ||
       (ctx->opt.omega_rule != 0 && ctx->opt.omega_rule != 1) ||
       (ctx->opt.persistent != 0 && ctx->opt.persistent != 1) || ctx->opt.wait_limit_ms < 1 ||
-      (ctx->opt.wait_test != 0 && ctx->opt.wait_test != 1)) {
+      (ctx->opt.wait_test != 0 && ctx->opt.wait_test != 1) || ctx->opt.step_rule != 0) {
     set_error("invalid options (eval_freq >= 1, precision 0/1, 1 <= fp32_screen <= 1e6, "
               "omega_rule 0/1, persistent 0/1, wait_limit_ms >= 1, wait_test 0/1, "
-              "method 0: batched solves use the averaged iteration)");
+              "method 0: batched solves use the averaged iteration, step_rule 0: the "
+              "constant step)");
     delete ctx;
     return PDHG_INVALID_ARG;
   }

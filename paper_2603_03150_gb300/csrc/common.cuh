@@ -129,6 +129,17 @@ struct Scalars {
   int32_t omega_rule;           // 0: smoothing with theta; 1: PID control of log omega
   double pid_kp, pid_ki, pid_kd;
   double pid_integral, pid_prev;  // sum of the PID errors so far, the last error
+  // adaptive step (step_rule 1, PDLP's rule): eta is the next attempt's step,
+  // eta_sum the accepted steps since the last restart, avg_w / avg_first the
+  // next attempt's averaging weight eta / (eta_sum + eta) and "no average yet",
+  // accept the last attempt's decision
+  int32_t step_rule;
+  int32_t accept;
+  int32_t avg_first;
+  int32_t pad2;
+  double avg_w;
+  double eta_sum;
+  long long step_rejects;
 };
 
 struct PowerState {

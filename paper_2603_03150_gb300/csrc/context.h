@@ -117,6 +117,12 @@ struct pdhg_ctx {
   float *b_t32 = nullptr, *c_t32 = nullptr;
   void *x = nullptr, *y = nullptr, *x_avg = nullptr, *y_avg = nullptr, *x_last = nullptr,
        *y_last = nullptr, *Ax = nullptr, *Ax_avg = nullptr, *Ax_last = nullptr;
+  // adaptive step (options.step_rule 1): the accepted state before an attempt
+  void *x_prev = nullptr, *x_avg_prev = nullptr, *y_prev = nullptr, *y_avg_prev = nullptr,
+       *Ax_prev = nullptr, *Ax_avg_prev = nullptr;
+  void *adapt_dx = nullptr, *adapt_Adx = nullptr;  // the attempt's move x+ - x and A~(x+ - x)
+  double* adapt_part = nullptr;  // [adapt_grid][3]
+  int adapt_grid = 0;
   double *xs64 = nullptr, *ys64 = nullptr, *out_n1 = nullptr, *out_n2 = nullptr,
          *out_m1 = nullptr, *report = nullptr, *sums = nullptr;
   Scalars* sc = nullptr;

@@ -105,6 +105,11 @@ __device__ inline void eval_restart(Scalars& sc, const double* tot, long long* l
     sc.tau = sc.eta / sc.omega;
     sc.sigma = sc.eta * sc.omega;
     sc.t = 0;
+    if (sc.step_rule) {  // the step-weighted averages restart too
+      sc.eta_sum = 0.0;
+      sc.avg_w = 1.0;
+      sc.avg_first = 1;
+    }
     sc.restarts += 1;
     sc.kkt_last = kc;
     sc.restart_pending = 1;

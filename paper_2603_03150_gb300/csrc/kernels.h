@@ -29,6 +29,11 @@ struct IterBuffers {
   const double *c_t64, *b_t64, *D_r, *D_c;  // float64 copies and scalings
   const double *Dr_inv, *Dc_inv;            // their reciprocals
   Scalars* sc;
+  // adaptive step (step_rule 1): the accepted state before an attempt, and
+  // the attempt's reduction partials [grid][3]
+  T *x_prev, *x_avg_prev, *y_prev, *y_avg_prev, *Ax_prev, *Ax_avg_prev;
+  T *adapt_dx, *adapt_Adx;  // the attempt's move x+ - x [n] and A~(x+ - x) [m]
+  double* adapt_part;
   double* partials;    // [grid][kEvalQ]
   double* split_q;     // [split groups of A^T][kEvalQ]
   long long* log_k;
@@ -51,6 +56,14 @@ template <typename T>
 void launch_primal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
 template <typename T>
 void launch_dual(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
+// adaptive step (options.step_rule 1): save the accepted state before attempt
+// i; after it, judge the attempt (and undo it when rejected)
+template <typename T>
+void launch_adapt_save(const IterBuffers<T>& B, int grid, cudaStream_t s);
+template <typename T>
+void launch_adapt_diff(const IterBuffers<T>& B, int grid, cudaStream_t s);
+template <typename T>
+void launch_adapt_step(const IterBuffers<T>& B, int grid, int i, cudaStream_t s);
 // evaluation after `chunk` iterations + on-device restart/termination rule
 template <typename T>
 void launch_eval(const IterBuffers<T>& B, const Launch& L, int chunk, cudaStream_t s);

@@ -250,6 +250,15 @@ static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
   B.Ax = (T*)ctx->Ax;
   B.Ax_avg = (T*)ctx->Ax_avg;
   B.Ax_last = (T*)ctx->Ax_last;
+  B.x_prev = (T*)ctx->x_prev;
+  B.x_avg_prev = (T*)ctx->x_avg_prev;
+  B.y_prev = (T*)ctx->y_prev;
+  B.y_avg_prev = (T*)ctx->y_avg_prev;
+  B.Ax_prev = (T*)ctx->Ax_prev;
+  B.Ax_avg_prev = (T*)ctx->Ax_avg_prev;
+  B.adapt_dx = (T*)ctx->adapt_dx;
+  B.adapt_Adx = (T*)ctx->adapt_Adx;
+  B.adapt_part = ctx->adapt_part;
   B.rho = ctx->opt.reflection;
   B.c_t64 = ctx->c_t64;
   B.b_t64 = ctx->b_t64;
@@ -309,7 +318,9 @@ static int dual_launches(const pdhg_ctx* ctx) { return ctx->pa.on ? 2 : 1; }
 // kernels of a chunk of `len` iterations: the half-steps, the evaluation, the
 // float64 check (float32-mixed) and the restart
 static long long chunk_launches(const pdhg_ctx* ctx, int len) {
-  return (long long)(prim_launches(ctx) + dual_launches(ctx)) * len + 2 +
+  // per attempt: save, the move, A~ times the move, judge, undo
+  const int adapt = ctx->opt.step_rule == 1 ? 5 : 0;
+  return (long long)(prim_launches(ctx) + dual_launches(ctx) + adapt) * len + 2 +
          (ctx->mixed ? kFp64CheckLaunches : 0);
 }
 
@@ -338,6 +349,7 @@ static void enqueue_chunk(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
   ctx->launches += chunk_launches(ctx, len);
   for (int i = 0; i < len; ++i) {
     const bool sample = timing && i == len / 2;
+    if (ctx->opt.step_rule == 1) launch_adapt_save<T>(B, ctx->adapt_grid, ctx->stream);
     if (sample) cudaEventRecordWithFlags(timing[0], ctx->stream, cudaEventRecordExternal);
     launch_prim_step<T>(ctx, B, i, sample ? timing[1] : nullptr);
     if (sample) {
@@ -346,6 +358,12 @@ static void enqueue_chunk(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
     }
     launch_dual_step<T>(ctx, B, i, sample ? timing[4] : nullptr);
     if (sample) cudaEventRecordWithFlags(timing[5], ctx->stream, cudaEventRecordExternal);
+    if (ctx->opt.step_rule == 1) {
+      launch_adapt_diff<T>(B, ctx->adapt_grid, ctx->stream);
+      launch_spmv<T>(ctx->sa.view, ctx->a_rp, ctx->a_col, B.a_val, B.adapt_dx, B.adapt_Adx,
+                     ctx->l_dual, ctx->stream);
+      launch_adapt_step<T>(B, ctx->adapt_grid, i, ctx->stream);
+    }
   }
   launch_eval<T>(B, ctx->l_eval, len, ctx->stream);
   if constexpr (sizeof(T) == 4) launch_fp64_check<T>(B, fp64_check_args(ctx), ctx->stream);
@@ -497,7 +515,7 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
     const int lay = ctx->opt.spmv_layout;
     int pw = 0, np = 0;
     const bool auto_panels = lay == 0 && ctx->opt.autotune && ctx->opt.tile_nnz == 0 &&
-                             ctx->nnz >= (int64_t(1) << 20);
+                             ctx->opt.step_rule == 0 && ctx->nnz >= (int64_t(1) << 20);
     if ((lay == 2 || auto_panels) && panel_shape(ctx, on_a, &pw, &np)) {
       DevPanel& dp = on_a ? ctx->pa : ctx->pt;
       CKS(build_panel_layout(ctx, on_a, &dp));
@@ -666,6 +684,15 @@ pdhg_status pdhg::alloc_arrays(pdhg_ctx* ctx) {
   void** vecs_m[] = {&ctx->y, &ctx->y_avg, &ctx->y_last, &ctx->Ax, &ctx->Ax_avg, &ctx->Ax_last};
   for (void** p : vecs_n) CKS(dalloc(ctx, (char**)p, es * n));
   for (void** p : vecs_m) CKS(dalloc(ctx, (char**)p, es * m));
+  if (ctx->opt.step_rule == 1 && !ctx->batch) {
+    for (void** p : {&ctx->x_prev, &ctx->x_avg_prev, &ctx->adapt_dx})
+      CKS(dalloc(ctx, (char**)p, es * n));
+    for (void** p : {&ctx->y_prev, &ctx->y_avg_prev, &ctx->Ax_prev, &ctx->Ax_avg_prev,
+                     &ctx->adapt_Adx})
+      CKS(dalloc(ctx, (char**)p, es * m));
+    ctx->adapt_grid = std::max(1, std::min(ctx->nsm * 4, (std::max(n, m) + 255) / 256));
+    CKS(dalloc(ctx, &ctx->adapt_part, 3 * (size_t)ctx->adapt_grid));
+  }
   CKS(dalloc(ctx, &ctx->xs64, n));
   CKS(dalloc(ctx, &ctx->ys64, m));
   CKS(dalloc(ctx, &ctx->out_n1, n));
@@ -922,6 +949,9 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     h.pid_kp = ctx->opt.pid_kp;
     h.pid_ki = ctx->opt.pid_ki;
     h.pid_kd = ctx->opt.pid_kd;
+    h.step_rule = ctx->opt.step_rule;
+    h.avg_w = 1.0;
+    h.avg_first = 1;
     h.log_cap = ctx->log_cap;
     h.status = PDHG_MAX_ITER;
     CK(cudaMemcpyAsync(ctx->sc, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
@@ -995,11 +1025,13 @@ extern "C" pdhg_status pdhg_create(pdhg_ctx** out, int32_t m, int32_t n, const i
       (ctx->opt.omega_rule != 0 && ctx->opt.omega_rule != 1) ||
       !std::isfinite(ctx->opt.pid_kp) || !std::isfinite(ctx->opt.pid_ki) ||
       !std::isfinite(ctx->opt.pid_kd) || ctx->opt.wait_limit_ms < 1 ||
-      (ctx->opt.wait_test != 0 && ctx->opt.wait_test != 1)) {
+      (ctx->opt.wait_test != 0 && ctx->opt.wait_test != 1) ||
+      (ctx->opt.step_rule != 0 && ctx->opt.step_rule != 1) ||
+      (ctx->opt.step_rule == 1 && (ctx->opt.method != 0 || ctx->opt.spmv_layout == 2))) {
     set_error("invalid options (eval_freq >= 1, ruiz_iters >= 0, precision 0/1, "
               "-8 <= tile_nnz <= 8192, method 0/1, 0 <= reflection <= 1, spmv_layout 0..2, "
               "panel_width >= 0, 1 <= fp32_screen <= 1e6, omega_rule 0/1, finite PID gains, "
-              "wait_limit_ms >= 1, wait_test 0/1)");
+              "wait_limit_ms >= 1, wait_test 0/1, step_rule 0/1 (1: method 0, not spmv_layout 2))");
     delete ctx;
     return PDHG_INVALID_ARG;
   }
@@ -1656,6 +1688,43 @@ extern "C" pdhg_status pdhg_set_pid_state(pdhg_ctx* ctx, double integral, double
   CK(cudaStreamSynchronize(ctx->stream));
   hs.pid_integral = integral;
   hs.pid_prev = prev_error;
+  CK(cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_step_state(pdhg_ctx* ctx, double* eta, double* eta_sum,
+                                           int64_t* rejects) {
+  g_last_error.clear();
+  if (!ctx || ctx->batch) {
+    set_error("need a single-LP context");
+    return PDHG_INVALID_ARG;
+  }
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (eta) *eta = hs.eta;
+  if (eta_sum) *eta_sum = hs.eta_sum;
+  if (rejects) *rejects = hs.step_rejects;
+  return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_set_step_state(pdhg_ctx* ctx, double eta, double eta_sum) {
+  g_last_error.clear();
+  if (!ctx || ctx->batch || !(eta > 0.0) || !std::isfinite(eta) || !(eta_sum >= 0.0) ||
+      !std::isfinite(eta_sum)) {
+    set_error("need a single-LP context, eta > 0 and eta_sum >= 0, both finite");
+    return PDHG_INVALID_ARG;
+  }
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  hs.eta = eta;
+  hs.eta_sum = eta_sum;
+  hs.tau = eta / hs.omega;
+  hs.sigma = eta * hs.omega;
+  hs.avg_w = eta / (eta_sum + eta);
+  hs.avg_first = eta_sum == 0.0 ? 1 : 0;
   CK(cudaMemcpyAsync(ctx->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return PDHG_OK;

@@ -64,6 +64,7 @@ class Options(ctypes.Structure):
         ("persistent", ctypes.c_int32),
         ("wait_limit_ms", ctypes.c_int32),
         ("wait_test", ctypes.c_int32),
+        ("step_rule", ctypes.c_int32),
     ]
 
 
@@ -103,6 +104,8 @@ _SIGS = {
     "pdhg_time_kernels": (_I32, [_P, _I32, _P]),
     "pdhg_get_pid_state": (_I32, [_P, _P, _P]),
     "pdhg_set_pid_state": (_I32, [_P, _D, _D]),
+    "pdhg_get_step_state": (_I32, [_P, _P, _P, _P]),
+    "pdhg_set_step_state": (_I32, [_P, _D, _D]),
     "pdhg_gather_floor": (_I32, [_P, _I32, _I32, _P]),
     "pdhg_batch_create": (_I32, [_PP, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options)]),
     "pdhg_batch_solve": (_I32, [_P, _D, _I64, _P]),
@@ -190,7 +193,7 @@ class Solver:
                  reflection: float = 1.0, spmv_layout: str = "auto", panel_width: int = 0,
                  fp32_screen: float = 1.0, omega_rule: str = "smooth", pid_kp: float = 0.99,
                  pid_ki: float = 0.01, pid_kd: float = 0.0, wait_limit_ms: int = 1000,
-                 wait_test: bool = False, verbose: bool = False):
+                 wait_test: bool = False, step_rule: str = "constant", verbose: bool = False):
         L = lib()
         o = Options()
         L.pdhg_default_options(ctypes.byref(o))
@@ -223,6 +226,9 @@ class Solver:
         o.pid_kp, o.pid_ki, o.pid_kd = pid_kp, pid_ki, pid_kd
         o.wait_limit_ms = wait_limit_ms
         o.wait_test = 1 if wait_test else 0
+        if step_rule not in ("constant", "adaptive"):
+            raise ValueError("step_rule must be 'constant' or 'adaptive'")
+        o.step_rule = 1 if step_rule == "adaptive" else 0
         o.verbose = 1 if verbose else 0
         self.m, self.n = int(m), int(n)
         self.device_io = device_io
@@ -317,7 +323,16 @@ class Solver:
         pi, pe = _D(), _D()
         _check(self._L.pdhg_get_pid_state(self._ctx, ctypes.byref(pi), ctypes.byref(pe)))
         d.update(pid_integral=pi.value, pid_prev=pe.value)
+        d.update(self.step_state())
         return d
+
+    def step_state(self):
+        """Adaptive step (step_rule 'adaptive'): the next attempt's step, the
+        accepted steps since the last restart, the rejected attempts."""
+        e, es, rj = _D(), _D(), _I64()
+        _check(self._L.pdhg_get_step_state(self._ctx, ctypes.byref(e), ctypes.byref(es),
+                                           ctypes.byref(rj)))
+        return dict(step_eta=e.value, eta_sum=es.value, step_rejects=rj.value)
 
     def set_state(self, st):
         sc = np.array([st["omega"], st["k"], st["t"], st["restarts"], st["kkt_last"],
@@ -330,6 +345,10 @@ class Solver:
         if "pid_integral" in st:
             _check(self._L.pdhg_set_pid_state(self._ctx, float(st["pid_integral"]),
                                               float(st.get("pid_prev", 0.0))),
+                   allow_positive=False)
+        if "step_eta" in st and st["step_eta"] > 0:
+            _check(self._L.pdhg_set_step_state(self._ctx, float(st["step_eta"]),
+                                               float(st.get("eta_sum", 0.0))),
                    allow_positive=False)
         if all(k in st for k in ("Ax", "Ax_avg", "Ax_last")):
             caches = [st[k] for k in ("Ax", "Ax_avg", "Ax_last")]
