@@ -249,7 +249,7 @@ def run_ours(args):
             s = pdhg.Solver(m, n, src["row_ptr"], src["col"], src["val"], src["b"], src["c"],
                             precision=precision, device_io=device_io, stream=stream.cuda_stream,
                             method=method or args.method, spmv_layout=args.layout,
-                            omega_rule=omega_rule or args.omega_rule)
+                            omega_rule=omega_rule or args.omega_rule, step_rule=args.step_rule)
             ev[1].record(stream)
             st = s.solve(EPS, args.max_iter)
             ev[2].record(stream)
@@ -317,7 +317,8 @@ def run_ours(args):
     # on the same workload and precision (not the default: the timed steps
     # above run the options the parity tests pin)
     variants = {}
-    if args.variant_steps > 0 and args.method == "averaged" and args.omega_rule == "smooth":
+    if (args.variant_steps > 0 and args.method == "averaged" and args.omega_rule == "smooth" and
+            args.step_rule == "constant"):
         for name, meth in (("pid", "averaged"), ("halpern_pid", "halpern")):
             rv = run_steps(args.precision, args.variant_steps, 1, method=meth, omega_rule="pid")
             variants[name] = dict(
@@ -341,7 +342,8 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         sk = pdhg.Solver(m, n, devt["row_ptr"], devt["col"], devt["val"], devt["b"], devt["c"],
                          precision=args.precision, device_io=True, stream=stream.cuda_stream,
-                         method=args.method, spmv_layout=args.layout, omega_rule=args.omega_rule)
+                         method=args.method, spmv_layout=args.layout, omega_rule=args.omega_rule,
+                         step_rule=args.step_rule)
         sk.solve(EPS, args.max_iter)
         kt = sk.time_kernels(args.kernel_reps)
         gf = {"dual": sk.gather_floor(True, 20), "primal": sk.gather_floor(False, 20)}
@@ -397,7 +399,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(lp, args.cpu_iters, args.method, args.omega_rule)
+        cpu = cpu_baseline(lp, args.cpu_iters, args.method, args.omega_rule, args.step_rule)
 
     if rank == 0:
         ms_step = total_ms / max(len(rec), 1)
@@ -409,6 +411,7 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[args.workload], "precision": args.precision +
                        ("_mixed (f64 norms, gap, restart rule, step/weight updates)" if args.precision == "fp32" else ""),
                        "eps_rel": EPS, "method": args.method, "omega_rule": args.omega_rule,
+                       "step_rule": args.step_rule,
                        "layout": args.layout,
                        "step": "create + solve to eps + get + warmstart_point (create and "
                                "solve also reported apart)",
@@ -818,14 +821,15 @@ def run_profile(args):
                           "schedule": s.schedule(), "launches": s.launch_count()}), flush=True)
 
 
-def cpu_baseline(lp, iters, method="averaged", omega_rule="smooth"):
+def cpu_baseline(lp, iters, method="averaged", omega_rule="smooth", step_rule="constant"):
     """The oracle as it stands, timed on this host: its set-up once (timed
     apart), then `iters` PDHG iterations (steady-state iterations per second)."""
     from oracle import pdhg_oracle as O
     t0 = time.perf_counter()
     S = O.setup(lp)
     t1 = time.perf_counter()
-    O.solve(lp, EPS, iters, opts=O.Options(method=method, omega_rule=omega_rule), S=S)
+    O.solve(lp, EPS, iters, opts=O.Options(method=method, omega_rule=omega_rule,
+                                           step_rule=step_rule), S=S)
     t2 = time.perf_counter()
     return {"value": round(iters / (t2 - t1), 3), "unit": "iter/s", "cores": 1, "kind": "oracle",
             "sample": f"{iters} iterations of the float64 numpy/scipy oracle on the same LP after "
@@ -850,8 +854,8 @@ def run_reference(args):
     for i in range(args.warmup + args.steps):
         t = time.perf_counter()
         k += args.ref_iters
-        r = O.solve(lp, EPS, k, opts=O.Options(method=args.method, omega_rule=args.omega_rule), S=S,
-                    state=st)
+        r = O.solve(lp, EPS, k, opts=O.Options(method=args.method, omega_rule=args.omega_rule,
+                                               step_rule=args.step_rule), S=S, state=st)
         st = r.state
         zs = np.maximum(0.0, S.c_t - S.At.T @ st.y)
         O.centered_start_point(st.x, zs)
@@ -891,6 +895,8 @@ def main():
                     help="PDHG iteration: restarted averaged (default) or reflected Halpern")
     ap.add_argument("--omega-rule", choices=["smooth", "pid"], default="smooth",
                     help="primal weight at restarts: smoothed ratio (default) or PID control")
+    ap.add_argument("--step-rule", choices=["constant", "adaptive"], default="constant",
+                    help="step size: constant (default) or PDLP's adaptive step")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--variant-steps", type=int, default=2,
                     help="steps of each PID primal-weight variant reported beside the default")
