@@ -18,8 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIBPATH = os.path.join(LIBDIR, "libpdhg.so")
 
-SOURCES = ["setup_kernels.cu", "iter_kernels.cu", "halpern.cu", "solver.cu", "noalloc.cu", "batch.cu",
-           "adjoint.cu", "diag.cu", "panel.cu"]
+SOURCES = ["setup_kernels.cu", "iter_kernels.cu", "halpern.cu", "adaptive.cu", "solver.cu", "noalloc.cu",
+           "batch.cu", "adjoint.cu", "diag.cu", "panel.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",

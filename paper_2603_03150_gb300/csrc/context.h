@@ -120,9 +120,11 @@ struct pdhg_ctx {
   // adaptive step (options.step_rule 1): the accepted state before an attempt
   void *x_prev = nullptr, *x_avg_prev = nullptr, *y_prev = nullptr, *y_avg_prev = nullptr,
        *Ax_prev = nullptr, *Ax_avg_prev = nullptr;
-  void *adapt_dx = nullptr, *adapt_Adx = nullptr;  // the attempt's move x+ - x and A~(x+ - x)
-  double* adapt_part = nullptr;  // [adapt_grid][3]
-  int adapt_grid = 0;
+  void* adapt_dx = nullptr;  // the attempt's move x+ - x
+  // the attempt's sums: per primal block, per split row of A~^T, per dual
+  // block (pairs), per split row of A~ (pairs); one allocation
+  double* adapt_sums = nullptr;
+  Launch l_aprim{}, l_adual{};  // the adaptive half-steps' launches
   double *xs64 = nullptr, *ys64 = nullptr, *out_n1 = nullptr, *out_n2 = nullptr,
          *out_m1 = nullptr, *report = nullptr, *sums = nullptr;
   Scalars* sc = nullptr;

@@ -22,10 +22,7 @@ __global__ void __launch_bounds__(BLOCK) k_primal(IterBuffers<T> B, int i) {
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const long long tt = B.sc->t + i;  // iterations since restart before this one
-  // averaging weight: uniform, or the step's share under the adaptive step
-  const bool ad = B.sc->step_rule != 0;
-  const T w = ad ? (T)B.sc->avg_w : (T)(1.0 / (double)(tt + 1));
-  PrimalEpi<T> epi{B.x, B.c_t, B.x_avg, (T)B.sc->tau, w, ad ? B.sc->avg_first != 0 : tt == 0};
+  PrimalEpi<T> epi{B.x, B.c_t, B.x_avg, (T)B.sc->tau, (T)(1.0 / (double)(tt + 1)), tt == 0};
   Gather<T, 1> g{{B.y}};
   run_sched<T, 1, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
 }
@@ -41,10 +38,8 @@ __global__ void __launch_bounds__(BLOCK) k_dual(IterBuffers<T> B, int i) {
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const long long tt = B.sc->t + i;
-  const bool ad = B.sc->step_rule != 0;
-  const T w = ad ? (T)B.sc->avg_w : (T)(1.0 / (double)(tt + 1));
-  DualEpi<T> epi{B.y,   B.b_t, B.Ax, B.y_avg, B.Ax_avg, (T)B.sc->sigma, w,
-                 ad ? B.sc->avg_first != 0 : tt == 0};
+  DualEpi<T> epi{B.y,   B.b_t, B.Ax, B.y_avg, B.Ax_avg, (T)B.sc->sigma, (T)(1.0 / (double)(tt + 1)),
+                 tt == 0};
   Gather<T, 1> g{{B.x}};
   run_sched<T, 1, BLOCK, E>(B.a_sched, B.a_rp, B.a_col, B.a_val, g, epi, smem);
 }
@@ -543,160 +538,12 @@ void launch_convert_f2d(const float* src, double* dst, int64_t len, cudaStream_t
   k_f2d<<<grid_for(len), 256, 0, s>>>(src, dst, len);
 }
 
-// ---------------------------------------------------------------------------
-// Adaptive step (options.step_rule 1, PDLP's rule): around each step attempt
-// the accepted state is saved, the attempt's move is reduced and judged, and
-// a rejected attempt is undone.  The attempt itself is the usual fused primal
-// and dual kernels with the step and averaging weight of the device state.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_adapt_save(IterBuffers<T> B) {
-  if (B.sc->done) return;
-  const int n = B.n, m = B.m, len = max(n, m);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len; j += gridDim.x * blockDim.x) {
-    if (j < n) {
-      B.x_prev[j] = B.x[j];
-      B.x_avg_prev[j] = B.x_avg[j];
-    }
-    if (j < m) {
-      B.y_prev[j] = B.y[j];
-      B.y_avg_prev[j] = B.y_avg[j];
-      B.Ax_prev[j] = B.Ax[j];
-      B.Ax_avg_prev[j] = B.Ax_avg[j];
-    }
-  }
-}
-
-// the attempt's move dx = x+ - x (A~ dx follows by the tile SpMV, so the
-// coupling term needs no difference of two nearly equal products)
-template <typename T>
-__global__ void k_adapt_diff(IterBuffers<T> B) {
-  if (B.sc->done) return;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < B.n; j += gridDim.x * blockDim.x)
-    B.adapt_dx[j] = B.x[j] - B.x_prev[j];
-}
-
-// sums over a 256-thread block in a fixed order; the result in thread 0
-__device__ __forceinline__ void block_sum3(double (&v)[3], double (*red)[8]) {
-#pragma unroll
-  for (int k = 0; k < 3; ++k) v[k] = warp_sum(v[k]);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) red[k][w] = v[k];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      double t = 0.0;
-      for (int q = 0; q < 8; ++q) t += red[k][q];
-      v[k] = t;
-    }
-}
-
-// ||x - x_prev||^2, ||y - y_prev||^2 and (y - y_prev)^T A~(x - x_prev) of
-// attempt i of the chunk; the last block to finish adds the blocks' sums in
-// block order and applies the rule: eta_max = (omega ||dx||^2 + ||dy||^2 /
-// omega) / (2 |dy^T A dx|), accept when eta <= eta_max, next step
-// min((1 - (j+1)^-0.3) eta_max, (1 + (j+1)^-0.6) eta), j = attempts so far
-// including this one; then the next attempt's tau, sigma and averaging weight
-template <typename T>
-__global__ void __launch_bounds__(256) k_adapt_step(IterBuffers<T> B, int i) {
-  if (B.sc->done) return;
-  __shared__ double red[3][8];
-  __shared__ int is_last;
-  const int n = B.n, m = B.m, len = max(n, m);
-  double v[3] = {0.0, 0.0, 0.0};
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len; j += gridDim.x * blockDim.x) {
-    if (j < n) {
-      const double d = (double)B.x[j] - (double)B.x_prev[j];
-      v[0] = fma(d, d, v[0]);
-    }
-    if (j < m) {
-      const double d = (double)B.y[j] - (double)B.y_prev[j];
-      v[1] = fma(d, d, v[1]);
-      v[2] = fma(d, (double)B.adapt_Adx[j], v[2]);
-    }
-  }
-  block_sum3(v, red);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) B.adapt_part[3 * blockIdx.x + k] = v[k];
-    __threadfence();
-    is_last = atomicAdd(&B.sc->ticket, 1) == (int)gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  double u[3] = {0.0, 0.0, 0.0};
-  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) u[k] += __ldcg(B.adapt_part + 3 * q + k);
-  block_sum3(u, red);
-  if (threadIdx.x != 0) return;
-  Scalars& sc = *B.sc;
-  sc.ticket = 0;
-  const double eta = sc.eta, om = sc.omega;
-  const double inter = fabs(u[2]);
-  const double num = om * u[0] + u[1] / om;
-  const double inf = __longlong_as_double(0x7ff0000000000000LL);
-  const double eta_max = inter > 0.0 ? num / (2.0 * inter) : inf;
-  const double j1 = (double)(sc.k + i + 1) + 1.0;
-  const double nxt = fmin((1.0 - pow(j1, -0.3)) * eta_max, (1.0 + pow(j1, -0.6)) * eta);
-  const bool acc = eta <= eta_max;
-  sc.accept = acc ? 1 : 0;
-  if (acc)
-    sc.eta_sum += eta;
-  else
-    sc.step_rejects += 1;
-  sc.eta = nxt;
-  sc.tau = nxt / om;
-  sc.sigma = nxt * om;
-  sc.avg_w = nxt / (sc.eta_sum + nxt);
-  sc.avg_first = sc.eta_sum == 0.0 ? 1 : 0;
-}
-
-template <typename T>
-__global__ void k_adapt_revert(IterBuffers<T> B) {
-  if (B.sc->done || B.sc->accept) return;
-  const int n = B.n, m = B.m, len = max(n, m);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len; j += gridDim.x * blockDim.x) {
-    if (j < n) {
-      B.x[j] = B.x_prev[j];
-      B.x_avg[j] = B.x_avg_prev[j];
-    }
-    if (j < m) {
-      B.y[j] = B.y_prev[j];
-      B.y_avg[j] = B.y_avg_prev[j];
-      B.Ax[j] = B.Ax_prev[j];
-      B.Ax_avg[j] = B.Ax_avg_prev[j];
-    }
-  }
-}
-
-template <typename T>
-void launch_adapt_save(const IterBuffers<T>& B, int grid, cudaStream_t s) {
-  k_adapt_save<T><<<grid, 256, 0, s>>>(B);
-}
-template <typename T>
-void launch_adapt_diff(const IterBuffers<T>& B, int grid, cudaStream_t s) {
-  k_adapt_diff<T><<<grid, 256, 0, s>>>(B);
-}
-template <typename T>
-void launch_adapt_step(const IterBuffers<T>& B, int grid, int i, cudaStream_t s) {
-  k_adapt_step<T><<<grid, 256, 0, s>>>(B, i);
-  k_adapt_revert<T><<<grid, 256, 0, s>>>(B);
-}
-
 // explicit instantiations
 #define PDHG_INST(T)                                                                        \
   template void launch_primal<T>(const IterBuffers<T>&, const Launch&, int, cudaStream_t); \
   template void launch_dual<T>(const IterBuffers<T>&, const Launch&, int, cudaStream_t);   \
   template void launch_eval<T>(const IterBuffers<T>&, const Launch&, int, cudaStream_t);   \
   template void launch_restart<T>(const IterBuffers<T>&, int, cudaStream_t);               \
-  template void launch_adapt_save<T>(const IterBuffers<T>&, int, cudaStream_t);             \
-  template void launch_adapt_step<T>(const IterBuffers<T>&, int, int, cudaStream_t);        \
-  template void launch_adapt_diff<T>(const IterBuffers<T>&, int, cudaStream_t);             \
   template void launch_spmv<T>(const SchedView&, const int32_t*, const int32_t*, const T*,  \
                                const T*, T*, const Launch&, cudaStream_t);
 PDHG_INST(float)

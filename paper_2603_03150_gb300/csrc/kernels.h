@@ -29,11 +29,14 @@ struct IterBuffers {
   const double *c_t64, *b_t64, *D_r, *D_c;  // float64 copies and scalings
   const double *Dr_inv, *Dc_inv;            // their reciprocals
   Scalars* sc;
-  // adaptive step (step_rule 1): the accepted state before an attempt, and
-  // the attempt's reduction partials [grid][3]
+  // adaptive step (step_rule 1): the accepted state before an attempt, the
+  // attempt's move x+ - x [n], and the sums of the attempt: ||dx||^2 per
+  // block of the primal kernel [adapt_np] and per split row of A~^T, then
+  // (||dy||^2, dy^T A~dx) per block of the dual kernel and per split row of A~
   T *x_prev, *x_avg_prev, *y_prev, *y_avg_prev, *Ax_prev, *Ax_avg_prev;
-  T *adapt_dx, *adapt_Adx;  // the attempt's move x+ - x [n] and A~(x+ - x) [m]
-  double* adapt_part;
+  T* adapt_dx;
+  double *adapt_pp, *adapt_sp, *adapt_pd, *adapt_sd;
+  int adapt_np;
   double* partials;    // [grid][kEvalQ]
   double* split_q;     // [split groups of A^T][kEvalQ]
   long long* log_k;
@@ -56,14 +59,6 @@ template <typename T>
 void launch_primal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
 template <typename T>
 void launch_dual(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
-// adaptive step (options.step_rule 1): save the accepted state before attempt
-// i; after it, judge the attempt (and undo it when rejected)
-template <typename T>
-void launch_adapt_save(const IterBuffers<T>& B, int grid, cudaStream_t s);
-template <typename T>
-void launch_adapt_diff(const IterBuffers<T>& B, int grid, cudaStream_t s);
-template <typename T>
-void launch_adapt_step(const IterBuffers<T>& B, int grid, int i, cudaStream_t s);
 // evaluation after `chunk` iterations + on-device restart/termination rule
 template <typename T>
 void launch_eval(const IterBuffers<T>& B, const Launch& L, int chunk, cudaStream_t s);
@@ -208,5 +203,18 @@ cudaError_t configure_halpern_kernels(size_t max_smem);
 // blocks per SM (which: 0/1 primal f32/f64, 2/3 dual f32/f64)
 int halpern_occupancy(int which, int e, size_t smem);
 size_t tile_smem(int nv, bool f32, int max_rows, int e);
+
+// ---- adaptive step (adaptive.cu) ------------------------------------------
+// attempt i of the chunk: the primal half-step saving the accepted state, the
+// dual half-step with the judge of the attempt, and the undo of a rejected one
+template <typename T>
+void launch_adapt_primal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
+template <typename T>
+void launch_adapt_dual(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
+template <typename T>
+void launch_adapt_revert(const IterBuffers<T>& B, int grid, cudaStream_t s);
+cudaError_t configure_adaptive_kernels(size_t max_smem);
+// blocks per SM (which: 0/1 primal f32/f64, 2/3 dual f32/f64)
+int adaptive_occupancy(int which, int e, size_t smem);
 
 }  // namespace pdhg

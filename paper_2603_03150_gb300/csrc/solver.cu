@@ -257,8 +257,13 @@ static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
   B.Ax_prev = (T*)ctx->Ax_prev;
   B.Ax_avg_prev = (T*)ctx->Ax_avg_prev;
   B.adapt_dx = (T*)ctx->adapt_dx;
-  B.adapt_Adx = (T*)ctx->adapt_Adx;
-  B.adapt_part = ctx->adapt_part;
+  if (ctx->adapt_sums) {
+    B.adapt_np = ctx->l_aprim.grid;
+    B.adapt_pp = ctx->adapt_sums;
+    B.adapt_sp = B.adapt_pp + ctx->l_aprim.grid;
+    B.adapt_pd = B.adapt_sp + ctx->st.view.ngroups;
+    B.adapt_sd = B.adapt_pd + 2 * (size_t)ctx->l_adual.grid;
+  }
   B.rho = ctx->opt.reflection;
   B.c_t64 = ctx->c_t64;
   B.b_t64 = ctx->b_t64;
@@ -313,15 +318,32 @@ static void launch_dual_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i,
     launch_dual<T>(B, ctx->l_dual, i, ctx->stream);
   if (between) cudaEventRecordWithFlags(between, ctx->stream, cudaEventRecordExternal);
 }
+// the half-steps a solve runs: the adaptive step's own kernels (its dual
+// half-step ends with the judge of the attempt, then the undo of a rejected
+// one), else the above
+template <typename T>
+static void launch_prim_half(pdhg_ctx* ctx, const IterBuffers<T>& B, int i,
+                             cudaEvent_t between = nullptr) {
+  if (ctx->opt.step_rule != 1) return launch_prim_step<T>(ctx, B, i, between);
+  launch_adapt_primal<T>(B, ctx->l_aprim, i, ctx->stream);
+  if (between) cudaEventRecordWithFlags(between, ctx->stream, cudaEventRecordExternal);
+}
+template <typename T>
+static void launch_dual_half(pdhg_ctx* ctx, const IterBuffers<T>& B, int i,
+                             cudaEvent_t between = nullptr) {
+  if (ctx->opt.step_rule != 1) return launch_dual_step<T>(ctx, B, i, between);
+  launch_adapt_dual<T>(B, ctx->l_adual, i, ctx->stream);
+  if (between) cudaEventRecordWithFlags(between, ctx->stream, cudaEventRecordExternal);
+  launch_adapt_revert<T>(B, ctx->restart_grid, ctx->stream);
+}
 static int prim_launches(const pdhg_ctx* ctx) { return ctx->pt.on ? 2 : 1; }
 static int dual_launches(const pdhg_ctx* ctx) { return ctx->pa.on ? 2 : 1; }
 // kernels of a chunk of `len` iterations: the half-steps, the evaluation, the
 // float64 check (float32-mixed) and the restart
 static long long chunk_launches(const pdhg_ctx* ctx, int len) {
-  // per attempt: save, the move, A~ times the move, judge, undo
-  const int adapt = ctx->opt.step_rule == 1 ? 5 : 0;
-  return (long long)(prim_launches(ctx) + dual_launches(ctx) + adapt) * len + 2 +
-         (ctx->mixed ? kFp64CheckLaunches : 0);
+  // adaptive step: the two half-steps and the undo of a rejected attempt
+  const int per = ctx->opt.step_rule == 1 ? 3 : prim_launches(ctx) + dual_launches(ctx);
+  return (long long)per * len + 2 + (ctx->mixed ? kFp64CheckLaunches : 0);
 }
 
 // what the float64 check of a float32-mixed candidate reads and writes
@@ -349,21 +371,14 @@ static void enqueue_chunk(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
   ctx->launches += chunk_launches(ctx, len);
   for (int i = 0; i < len; ++i) {
     const bool sample = timing && i == len / 2;
-    if (ctx->opt.step_rule == 1) launch_adapt_save<T>(B, ctx->adapt_grid, ctx->stream);
     if (sample) cudaEventRecordWithFlags(timing[0], ctx->stream, cudaEventRecordExternal);
-    launch_prim_step<T>(ctx, B, i, sample ? timing[1] : nullptr);
+    launch_prim_half<T>(ctx, B, i, sample ? timing[1] : nullptr);
     if (sample) {
       cudaEventRecordWithFlags(timing[2], ctx->stream, cudaEventRecordExternal);
       cudaEventRecordWithFlags(timing[3], ctx->stream, cudaEventRecordExternal);
     }
-    launch_dual_step<T>(ctx, B, i, sample ? timing[4] : nullptr);
+    launch_dual_half<T>(ctx, B, i, sample ? timing[4] : nullptr);
     if (sample) cudaEventRecordWithFlags(timing[5], ctx->stream, cudaEventRecordExternal);
-    if (ctx->opt.step_rule == 1) {
-      launch_adapt_diff<T>(B, ctx->adapt_grid, ctx->stream);
-      launch_spmv<T>(ctx->sa.view, ctx->a_rp, ctx->a_col, B.a_val, B.adapt_dx, B.adapt_Adx,
-                     ctx->l_dual, ctx->stream);
-      launch_adapt_step<T>(B, ctx->adapt_grid, i, ctx->stream);
-    }
   }
   launch_eval<T>(B, ctx->l_eval, len, ctx->stream);
   if constexpr (sizeof(T) == 4) launch_fp64_check<T>(B, fp64_check_args(ctx), ctx->stream);
@@ -570,6 +585,21 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
+// Launches of the adaptive half-steps on the tuned schedules (the dual
+// gathers x+ and the move together) and the attempt's sums: one per primal
+// block and split row of A~^T, two per dual block and split row of A~.
+static pdhg_status adaptive_launches(pdhg_ctx* ctx) {
+  if (ctx->opt.step_rule != 1 || ctx->batch) return PDHG_OK;
+  const bool mx = ctx->mixed;
+  const SchedView &A = ctx->sa.view, &T = ctx->st.view;
+  const size_t sp = smem_for(0, mx, T.max_rows, T.e), sd = smem_for(1, mx, A.max_rows, A.e);
+  ctx->l_aprim = Launch{std::max(1, std::min(T.ntiles, ctx->nsm * adaptive_occupancy(mx ? 0 : 1, T.e, sp))), sp};
+  ctx->l_adual = Launch{std::max(1, std::min(A.ntiles, ctx->nsm * adaptive_occupancy(mx ? 2 : 3, A.e, sd))), sd};
+  const size_t len = (size_t)ctx->l_aprim.grid + T.ngroups + 2 * ((size_t)ctx->l_adual.grid + A.ngroups);
+  CKS(dalloc(ctx, &ctx->adapt_sums, len));
+  return PDHG_OK;
+}
+
 static pdhg_status build_graphs(pdhg_ctx* ctx) {
   const int F = ctx->opt.eval_freq;
   for (int g = 0; g < 2; ++g) {
@@ -646,6 +676,7 @@ pdhg_status pdhg::setup_device(pdhg_ctx* ctx) {
   }
   CK(configure_tile_kernels(ctx->smem_optin));
   CK(configure_halpern_kernels(ctx->smem_optin));
+  CK(configure_adaptive_kernels(ctx->smem_optin));
   CK(configure_panel_kernels(ctx->smem_optin));
   CK(configure_setup_kernels(ctx->smem_optin));
 
@@ -687,11 +718,8 @@ pdhg_status pdhg::alloc_arrays(pdhg_ctx* ctx) {
   if (ctx->opt.step_rule == 1 && !ctx->batch) {
     for (void** p : {&ctx->x_prev, &ctx->x_avg_prev, &ctx->adapt_dx})
       CKS(dalloc(ctx, (char**)p, es * n));
-    for (void** p : {&ctx->y_prev, &ctx->y_avg_prev, &ctx->Ax_prev, &ctx->Ax_avg_prev,
-                     &ctx->adapt_Adx})
+    for (void** p : {&ctx->y_prev, &ctx->y_avg_prev, &ctx->Ax_prev, &ctx->Ax_avg_prev})
       CKS(dalloc(ctx, (char**)p, es * m));
-    ctx->adapt_grid = std::max(1, std::min(ctx->nsm * 4, (std::max(n, m) + 255) / 256));
-    CKS(dalloc(ctx, &ctx->adapt_part, 3 * (size_t)ctx->adapt_grid));
   }
   CKS(dalloc(ctx, &ctx->xs64, n));
   CKS(dalloc(ctx, &ctx->ys64, m));
@@ -976,6 +1004,7 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
 
   stage("scalars");
   CKS(tune_schedules(ctx));
+  CKS(adaptive_launches(ctx));
   stage("schedule tuning");
   CKS(polling_resources(ctx));
   stage("polling resources");
@@ -1580,13 +1609,14 @@ static pdhg_status time_kernels_impl(pdhg_ctx* ctx, int reps, double* ms) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   // which: 0 primal half-step, 1 dual, 2 iteration, 3 primal panel SpMV, 4 dual panel SpMV
+  // (the half-steps the solve runs: with the adaptive step, its own kernels)
   auto run = [&](int which) {
     switch (which) {
-      case 0: launch_prim_step<T>(ctx, B, 0); break;
-      case 1: launch_dual_step<T>(ctx, B, 0); break;
+      case 0: launch_prim_half<T>(ctx, B, 0); break;
+      case 1: launch_dual_half<T>(ctx, B, 0); break;
       case 2:
-        launch_prim_step<T>(ctx, B, 0);
-        launch_dual_step<T>(ctx, B, 0);
+        launch_prim_half<T>(ctx, B, 0);
+        launch_dual_half<T>(ctx, B, 0);
         break;
       case 3:
         if constexpr (sizeof(T) == 4) launch_panel_spmv_only(B, ctx->pt.view, false, ctx->opt.method, ctx->stream);
@@ -1602,8 +1632,9 @@ static pdhg_status time_kernels_impl(pdhg_ctx* ctx, int reps, double* ms) {
     ms[which] = 0.0;
     if ((which == 3 && !(ctx->mixed && ctx->pt.on)) || (which == 4 && !(ctx->mixed && ctx->pa.on)))
       continue;
-    const long long per = which == 0 ? prim_launches(ctx) : which == 1 ? dual_launches(ctx)
-                          : which == 2 ? prim_launches(ctx) + dual_launches(ctx) : 1;
+    const bool ad = ctx->opt.step_rule == 1;
+    const long long np = ad ? 1 : prim_launches(ctx), nd = ad ? 2 : dual_launches(ctx);
+    const long long per = which == 0 ? np : which == 1 ? nd : which == 2 ? np + nd : 1;
     ctx->launches += per * (warm + reps);
     for (int it = 0; it < warm + reps; ++it) {
       if (it == warm) cudaEventRecord(e0, ctx->stream);
