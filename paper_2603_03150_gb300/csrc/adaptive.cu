@@ -10,9 +10,10 @@
 // accepted iterate by its step.
 //
 // K1 (rows of A~^T): the primal epilogue saves x and x_avg, writes x+, the
-//   move dx and the new average, and sums dx_j^2.
-// K2 (rows of A~): x+ and dx are gathered together, so one pass over A~
-//   gives h = A~x+ and A~dx; the epilogue saves y, y_avg, A~x, A~x_avg,
+//   new average and the pair (x+_j, dx_j) into an interleaved vector, and
+//   sums dx_j^2.
+// K2 (rows of A~): the pairs are gathered with one load per nonzero, so one
+//   pass over A~ gives h = A~x+ and A~dx; the epilogue saves y, y_avg, A~x, A~x_avg,
 //   writes the dual step, and sums dy_i^2 and dy_i (A~dx)_i.  The last block
 //   adds every block's sums in block order and applies the rule above.
 // K3: when the attempt was rejected, the saved state is copied back.
@@ -35,7 +36,7 @@ struct AdaptPrimalEpi {
   T* __restrict__ x_avg;
   T* __restrict__ x_prev;
   T* __restrict__ x_avg_prev;
-  T* __restrict__ dx;
+  T* __restrict__ xdx;  // (x+_j, dx_j) at 2j, 2j + 1
   double* __restrict__ split_rec;  // one per split group of A~^T
   T tau, w;
   bool first;
@@ -48,7 +49,10 @@ struct AdaptPrimalEpi {
     x_avg_prev[j] = xa;
     x[j] = xn;
     x_avg[j] = first ? xn : xa + (xn - xa) * w;
-    dx[j] = d;
+    if constexpr (sizeof(T) == 4)
+      reinterpret_cast<float2*>(xdx)[j] = make_float2(xn, d);
+    else
+      reinterpret_cast<double2*>(xdx)[j] = make_double2(xn, d);
     if (group < 0)
       acc = fmadd(d, d, acc);
     else
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(BLOCK) k_aprimal(IterBuffers<T> B, int i) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[BLOCK / 32];
   __shared__ double out[1];
-  AdaptPrimalEpi<T> epi{B.x,      B.c_t, B.x_avg, B.x_prev, B.x_avg_prev, B.adapt_dx, B.adapt_sp,
+  AdaptPrimalEpi<T> epi{B.x,      B.c_t, B.x_avg, B.x_prev, B.x_avg_prev, B.adapt_xdx, B.adapt_sp,
                         (T)B.sc->tau, (T)B.sc->avg_w, B.sc->avg_first != 0, T(0)};
   Gather<T, 1> g{{B.y}};
   run_sched<T, 1, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(BLOCK) k_adual(IterBuffers<T> B, int i) {
                       B.sc->avg_first != 0,
                       T(0),
                       T(0)};
-  Gather<T, 2> g{{B.x, B.adapt_dx}};
+  GatherPair<T> g{B.adapt_xdx};
   run_sched<T, 2, BLOCK, E>(B.a_sched, B.a_rp, B.a_col, B.a_val, g, epi, smem);
   double mine[2] = {(double)epi.dy2, (double)epi.cross};
   block_sum<BLOCK, 2>(mine, out, red);

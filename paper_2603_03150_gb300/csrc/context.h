@@ -120,7 +120,7 @@ struct pdhg_ctx {
   // adaptive step (options.step_rule 1): the accepted state before an attempt
   void *x_prev = nullptr, *x_avg_prev = nullptr, *y_prev = nullptr, *y_avg_prev = nullptr,
        *Ax_prev = nullptr, *Ax_avg_prev = nullptr;
-  void* adapt_dx = nullptr;  // the attempt's move x+ - x
+  void* adapt_xdx = nullptr;  // the attempt's (x+_j, x+_j - x_j), interleaved [2n]
   // the attempt's sums: per primal block, per split row of A~^T, per dual
   // block (pairs), per split row of A~ (pairs); one allocation
   double* adapt_sums = nullptr;

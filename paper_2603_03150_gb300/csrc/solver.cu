@@ -256,7 +256,7 @@ static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
   B.y_avg_prev = (T*)ctx->y_avg_prev;
   B.Ax_prev = (T*)ctx->Ax_prev;
   B.Ax_avg_prev = (T*)ctx->Ax_avg_prev;
-  B.adapt_dx = (T*)ctx->adapt_dx;
+  B.adapt_xdx = (T*)ctx->adapt_xdx;
   if (ctx->adapt_sums) {
     B.adapt_np = ctx->l_aprim.grid;
     B.adapt_pp = ctx->adapt_sums;
@@ -716,8 +716,9 @@ pdhg_status pdhg::alloc_arrays(pdhg_ctx* ctx) {
   for (void** p : vecs_n) CKS(dalloc(ctx, (char**)p, es * n));
   for (void** p : vecs_m) CKS(dalloc(ctx, (char**)p, es * m));
   if (ctx->opt.step_rule == 1 && !ctx->batch) {
-    for (void** p : {&ctx->x_prev, &ctx->x_avg_prev, &ctx->adapt_dx})
+    for (void** p : {&ctx->x_prev, &ctx->x_avg_prev})
       CKS(dalloc(ctx, (char**)p, es * n));
+    CKS(dalloc(ctx, (char**)&ctx->adapt_xdx, es * 2 * (size_t)n));
     for (void** p : {&ctx->y_prev, &ctx->y_avg_prev, &ctx->Ax_prev, &ctx->Ax_avg_prev})
       CKS(dalloc(ctx, (char**)p, es * m));
   }

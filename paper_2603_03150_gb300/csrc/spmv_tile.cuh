@@ -29,9 +29,32 @@
 
 namespace pdhg {
 
+// The vectors a tile kernel gathers: load(c, o) gives entry c of each.
 template <typename T, int NV>
 struct Gather {
   const T* v[NV];
+  __device__ __forceinline__ void load(int c, T (&o)[NV]) const {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) o[q] = __ldg(v[q] + c);
+  }
+};
+
+// Two vectors stored interleaved (entry c of each at p[2c], p[2c + 1]): one
+// 8- or 16-byte load per nonzero instead of two scattered ones.
+template <typename T>
+struct GatherPair {
+  const T* p;
+  __device__ __forceinline__ void load(int c, T (&o)[2]) const {
+    if constexpr (sizeof(T) == 4) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(p) + c);
+      o[0] = q.x;
+      o[1] = q.y;
+    } else {
+      const double2 q = __ldg(reinterpret_cast<const double2*>(p) + c);
+      o[0] = q.x;
+      o[1] = q.y;
+    }
+  }
 };
 
 // Nonzeros a tile may hold when each of BLOCK threads owns E of them: the
@@ -200,10 +223,10 @@ __host__ __device__ constexpr typename WindowWord<E>::type window_word(int first
 // A thread's window of E nonzeros is loaded, gathered and walked in steps of
 // EC = 8 (E = 16, 32: the per-tile work - descriptor, carry scan, barriers -
 // is shared by more nonzeros at the register cost of E = 8).
-template <typename T, int NV, int BLOCK, int E, class Epi>
+template <typename T, int NV, int BLOCK, int E, class Epi, class Gv>
 __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __restrict__ /*row_ptr*/,
                                           const int32_t* __restrict__ col,
-                                          const T* __restrict__ val, const Gather<T, NV>& g,
+                                          const T* __restrict__ val, const Gv& g,
                                           Epi& epi, unsigned char* smem) {
   static_assert(E % 4 == 0 && E <= 32, "E must be a multiple of 4, at most 32");
   using W = typename WindowWord<E>::type;
@@ -283,8 +306,15 @@ __device__ __forceinline__ void run_tiles(const SchedView& S, const int32_t* __r
       for (int e = 0; e < EC; ++e) {
         const int k = wc + e;
         const bool in = k >= nzb && k < nze;
+        T q[NV];
+        if (in) {
+          g.load(cidx[e], q);
+        } else {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) gv[v][e] = in ? __ldg(g.v[v] + cidx[e]) : T(0);
+          for (int v = 0; v < NV; ++v) q[v] = T(0);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) gv[v][e] = q[v];
       }
 #pragma unroll
       for (int e = 0; e < EC; ++e) {
@@ -350,10 +380,10 @@ __host__ __device__ constexpr size_t tile_smem_bytes(int max_rows) {
 // (two block barriers per tile, no row search or carry scan).  Split tiles
 // reduce over the whole block as above.
 // ---------------------------------------------------------------------------
-template <typename T, int NV, int BLOCK, int G, class Epi>
+template <typename T, int NV, int BLOCK, int G, class Epi, class Gv>
 __device__ __forceinline__ void run_tiles_vec(const SchedView& S, const int32_t* __restrict__ row_ptr,
                                               const int32_t* __restrict__ col,
-                                              const T* __restrict__ val, const Gather<T, NV>& g,
+                                              const T* __restrict__ val, const Gv& g,
                                               Epi& epi, unsigned char* smem) {
   static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "G must be a power of two <= 32");
   constexpr int NW = BLOCK / 32;
@@ -374,8 +404,10 @@ __device__ __forceinline__ void run_tiles_vec(const SchedView& S, const int32_t*
       for (int k = tl.nz_begin + tid; k < tl.nz_end; k += BLOCK) {
         const T a = ld_stream(val + k, pol);
         const int c = ld_stream(col + k, pol);
+        T q[NV];
+        g.load(c, q);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) s[v] += a * __ldg(g.v[v] + c);
+        for (int v = 0; v < NV; ++v) s[v] += a * q[v];
       }
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -424,8 +456,10 @@ __device__ __forceinline__ void run_tiles_vec(const SchedView& S, const int32_t*
         for (int k = __ldg(row_ptr + r) + gl; k < e; k += G) {
           const T a = ld_stream(val + k, pol);
           const int c = ld_stream(col + k, pol);
+          T q[NV];
+          g.load(c, q);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) s[v] += a * __ldg(g.v[v] + c);
+          for (int v = 0; v < NV; ++v) s[v] += a * q[v];
         }
       }
 #pragma unroll
@@ -450,10 +484,10 @@ __device__ __forceinline__ void run_tiles_vec(const SchedView& S, const int32_t*
 
 // Schedule variant V: V > 0 segmented with E = V nonzeros per thread,
 // V < 0 vector with G = -V lanes per row.
-template <typename T, int NV, int BLOCK, int V, class Epi>
+template <typename T, int NV, int BLOCK, int V, class Epi, class Gv>
 __device__ __forceinline__ void run_sched(const SchedView& S, const int32_t* __restrict__ row_ptr,
                                           const int32_t* __restrict__ col,
-                                          const T* __restrict__ val, const Gather<T, NV>& g,
+                                          const T* __restrict__ val, const Gv& g,
                                           Epi& epi, unsigned char* smem) {
   if constexpr (V > 0)
     run_tiles<T, NV, BLOCK, V>(S, row_ptr, col, val, g, epi, smem);
