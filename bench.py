@@ -815,7 +815,8 @@ def run_profile(args):
     lp = make_lp(args.workload)
     layout = args.layout
     with pdhg.Solver.from_lp(lp, precision=args.precision, spmv_layout=layout,
-                             method=args.method) as s:
+                             method=args.method, omega_rule=args.omega_rule,
+                             step_rule=args.step_rule) as s:
         s.solve(0.0, args.profile_run)
         print(json.dumps({"iters": s.info(violation=False)["iters"], "layout": s.layout(),
                           "schedule": s.schedule(), "launches": s.launch_count()}), flush=True)

@@ -9,14 +9,16 @@
 // leaves z and the running averages as they were.  The averages weight each
 // accepted iterate by its step.
 //
-// K1 (rows of A~^T): the primal epilogue saves x and x_avg, writes x+, the
-//   new average and the pair (x+_j, dx_j) into an interleaved vector, and
-//   sums dx_j^2.
-// K2 (rows of A~): the pairs are gathered with one load per nonzero, so one
-//   pass over A~ gives h = A~x+ and A~dx; the epilogue saves y, y_avg, A~x, A~x_avg,
+// K1 (rows of A~^T): the primal epilogue writes x+, the new average, the
+//   pair (x+_j, x_j) into an interleaved vector (the accepted x is kept
+//   there) and the saved x_avg, and sums dx_j^2.
+// K2 (rows of A~): the pairs are gathered with one load per nonzero and
+//   dx_j = x+_j - x_j formed as in K1, so one pass over A~ gives h = A~x+
+//   and A~dx; the epilogue saves y, y_avg, A~x, A~x_avg,
 //   writes the dual step, and sums dy_i^2 and dy_i (A~dx)_i.  The last block
 //   adds every block's sums in block order and applies the rule above.
-// K3: when the attempt was rejected, the saved state is copied back.
+// K3: when the attempt was rejected, the saved state is copied back (x from
+//   the pairs).
 //
 // A thread accumulates its rows in the iteration precision (in float32-mixed
 // contexts the float64 pipe would bound the epilogue); blocks' sums are
@@ -34,9 +36,8 @@ struct AdaptPrimalEpi {
   T* __restrict__ x;
   const T* __restrict__ c;
   T* __restrict__ x_avg;
-  T* __restrict__ x_prev;
   T* __restrict__ x_avg_prev;
-  T* __restrict__ xdx;  // (x+_j, dx_j) at 2j, 2j + 1
+  T* __restrict__ xx;  // (x+_j, x_j) at 2j, 2j + 1
   double* __restrict__ split_rec;  // one per split group of A~^T
   T tau, w;
   bool first;
@@ -45,18 +46,27 @@ struct AdaptPrimalEpi {
     const T xo = x[j], xa = x_avg[j];
     const T xn = fmax(T(0), xo - tau * (c[j] - s[0]));
     const T d = xn - xo;
-    x_prev[j] = xo;
     x_avg_prev[j] = xa;
     x[j] = xn;
     x_avg[j] = first ? xn : xa + (xn - xa) * w;
     if constexpr (sizeof(T) == 4)
-      reinterpret_cast<float2*>(xdx)[j] = make_float2(xn, d);
+      reinterpret_cast<float2*>(xx)[j] = make_float2(xn, xo);
     else
-      reinterpret_cast<double2*>(xdx)[j] = make_double2(xn, d);
+      reinterpret_cast<double2*>(xx)[j] = make_double2(xn, xo);
     if (group < 0)
       acc = fmadd(d, d, acc);
     else
       split_rec[group] = (double)d * (double)d;
+  }
+};
+
+// x+_j and dx_j = x+_j - x_j (the same rounding as K1's) from one load of the pair
+template <typename T>
+struct GatherMove {
+  GatherPair<T> pair;
+  __device__ __forceinline__ void load(int c, T (&o)[2]) const {
+    pair.load(c, o);
+    o[1] = o[0] - o[1];
   }
 };
 
@@ -106,8 +116,9 @@ __global__ void __launch_bounds__(BLOCK) k_aprimal(IterBuffers<T> B, int i) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[BLOCK / 32];
   __shared__ double out[1];
-  AdaptPrimalEpi<T> epi{B.x,      B.c_t, B.x_avg, B.x_prev, B.x_avg_prev, B.adapt_xdx, B.adapt_sp,
-                        (T)B.sc->tau, (T)B.sc->avg_w, B.sc->avg_first != 0, T(0)};
+  AdaptPrimalEpi<T> epi{B.x,          B.c_t,          B.x_avg,               B.x_avg_prev, B.adapt_xx,
+                        B.adapt_sp,   (T)B.sc->tau,   (T)B.sc->avg_w,        B.sc->avg_first != 0,
+                        T(0)};
   Gather<T, 1> g{{B.y}};
   run_sched<T, 1, BLOCK, E>(B.t_sched, B.t_rp, B.t_col, B.t_val, g, epi, smem);
   double mine[1] = {(double)epi.acc};
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(BLOCK) k_adual(IterBuffers<T> B, int i) {
                       B.sc->avg_first != 0,
                       T(0),
                       T(0)};
-  GatherPair<T> g{B.adapt_xdx};
+  GatherMove<T> g{{B.adapt_xx}};
   run_sched<T, 2, BLOCK, E>(B.a_sched, B.a_rp, B.a_col, B.a_val, g, epi, smem);
   double mine[2] = {(double)epi.dy2, (double)epi.cross};
   block_sum<BLOCK, 2>(mine, out, red);
@@ -185,7 +196,7 @@ __global__ void k_adapt_revert(IterBuffers<T> B) {
   const int n = B.n, m = B.m, len = max(n, m);
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len; j += gridDim.x * blockDim.x) {
     if (j < n) {
-      B.x[j] = B.x_prev[j];
+      B.x[j] = B.adapt_xx[2 * (size_t)j + 1];
       B.x_avg[j] = B.x_avg_prev[j];
     }
     if (j < m) {

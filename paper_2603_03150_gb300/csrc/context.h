@@ -118,9 +118,10 @@ struct pdhg_ctx {
   void *x = nullptr, *y = nullptr, *x_avg = nullptr, *y_avg = nullptr, *x_last = nullptr,
        *y_last = nullptr, *Ax = nullptr, *Ax_avg = nullptr, *Ax_last = nullptr;
   // adaptive step (options.step_rule 1): the accepted state before an attempt
-  void *x_prev = nullptr, *x_avg_prev = nullptr, *y_prev = nullptr, *y_avg_prev = nullptr,
-       *Ax_prev = nullptr, *Ax_avg_prev = nullptr;
-  void* adapt_xdx = nullptr;  // the attempt's (x+_j, x+_j - x_j), interleaved [2n]
+  // (its x in adapt_xx)
+  void *x_avg_prev = nullptr, *y_prev = nullptr, *y_avg_prev = nullptr, *Ax_prev = nullptr,
+       *Ax_avg_prev = nullptr;
+  void* adapt_xx = nullptr;  // the attempt's (x+_j, x_j), interleaved [2n]
   // the attempt's sums: per primal block, per split row of A~^T, per dual
   // block (pairs), per split row of A~ (pairs); one allocation
   double* adapt_sums = nullptr;

@@ -29,13 +29,14 @@ struct IterBuffers {
   const double *c_t64, *b_t64, *D_r, *D_c;  // float64 copies and scalings
   const double *Dr_inv, *Dc_inv;            // their reciprocals
   Scalars* sc;
-  // adaptive step (step_rule 1): the accepted state before an attempt, the
-  // attempt's iterate and move interleaved, (x+_j, x+_j - x_j) at 2j, 2j + 1
-  // [2n], and the sums of the attempt: ||dx||^2 per block of the primal
-  // kernel [adapt_np] and per split row of A~^T, then (||dy||^2, dy^T A~dx)
-  // per block of the dual kernel and per split row of A~
-  T *x_prev, *x_avg_prev, *y_prev, *y_avg_prev, *Ax_prev, *Ax_avg_prev;
-  T* adapt_xdx;
+  // adaptive step (step_rule 1): the accepted state before an attempt (x in
+  // adapt_xx), the attempt's iterate and the accepted one interleaved,
+  // (x+_j, x_j) at 2j, 2j + 1 [2n], and the sums of the attempt: ||dx||^2
+  // per block of the primal kernel [adapt_np] and per split row of A~^T,
+  // then (||dy||^2, dy^T A~dx) per block of the dual kernel and per split
+  // row of A~
+  T *x_avg_prev, *y_prev, *y_avg_prev, *Ax_prev, *Ax_avg_prev;
+  T* adapt_xx;
   double *adapt_pp, *adapt_sp, *adapt_pd, *adapt_sd;
   int adapt_np;
   double* partials;    // [grid][kEvalQ]

@@ -250,13 +250,12 @@ static IterBuffers<T> iter_buffers(pdhg_ctx* ctx) {
   B.Ax = (T*)ctx->Ax;
   B.Ax_avg = (T*)ctx->Ax_avg;
   B.Ax_last = (T*)ctx->Ax_last;
-  B.x_prev = (T*)ctx->x_prev;
   B.x_avg_prev = (T*)ctx->x_avg_prev;
   B.y_prev = (T*)ctx->y_prev;
   B.y_avg_prev = (T*)ctx->y_avg_prev;
   B.Ax_prev = (T*)ctx->Ax_prev;
   B.Ax_avg_prev = (T*)ctx->Ax_avg_prev;
-  B.adapt_xdx = (T*)ctx->adapt_xdx;
+  B.adapt_xx = (T*)ctx->adapt_xx;
   if (ctx->adapt_sums) {
     B.adapt_np = ctx->l_aprim.grid;
     B.adapt_pp = ctx->adapt_sums;
@@ -716,9 +715,8 @@ pdhg_status pdhg::alloc_arrays(pdhg_ctx* ctx) {
   for (void** p : vecs_n) CKS(dalloc(ctx, (char**)p, es * n));
   for (void** p : vecs_m) CKS(dalloc(ctx, (char**)p, es * m));
   if (ctx->opt.step_rule == 1 && !ctx->batch) {
-    for (void** p : {&ctx->x_prev, &ctx->x_avg_prev})
-      CKS(dalloc(ctx, (char**)p, es * n));
-    CKS(dalloc(ctx, (char**)&ctx->adapt_xdx, es * 2 * (size_t)n));
+    CKS(dalloc(ctx, (char**)&ctx->x_avg_prev, es * n));
+    CKS(dalloc(ctx, (char**)&ctx->adapt_xx, es * 2 * (size_t)n));
     for (void** p : {&ctx->y_prev, &ctx->y_avg_prev, &ctx->Ax_prev, &ctx->Ax_avg_prev})
       CKS(dalloc(ctx, (char**)p, es * m));
   }
