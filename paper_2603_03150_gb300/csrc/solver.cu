@@ -198,14 +198,19 @@ Launch pdhg::make_launch(pdhg_ctx* ctx, int occ_kind, int e, size_t smem, int nt
 // Float64 schedules (report, Algorithm 1, power iteration) and reduction
 // scratch sized for any iteration schedule the tuner may pick.
 static pdhg_status fixed_schedules(pdhg_ctx* ctx) {
-  int64_t long_rows = 0;  // rows that any candidate schedule could split
+  // rows that any candidate schedule could split: longer than the smallest
+  // tile capacity the tuner may use (a forced options.tile_nnz below the
+  // full capacity of 8 nonzeros per thread splits shorter rows too)
+  const int cap_min = ctx->opt.tile_nnz > 0 ? std::min(ctx->opt.tile_nnz, tile_capacity(kBlock, 8))
+                                            : tile_capacity(kBlock, 8);
+  int64_t long_rows = 0;
   for (int which = 0; which < 2; ++which) {
     const bool on_a = which == 0;
     const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
     const int nrows = on_a ? ctx->m : ctx->n;
     HostSched h = build_sched(rp.data(), nrows, kFixedE);
     CKS(upload_sched(ctx, h, on_a ? &ctx->sa8 : &ctx->st8, on_a ? ctx->a_rp : ctx->t_rp));
-    for (int r = 0; r < nrows; ++r) long_rows += (rp[r + 1] - rp[r]) > tile_capacity(kBlock, 8);
+    for (int r = 0; r < nrows; ++r) long_rows += (rp[r + 1] - rp[r]) > cap_min;
   }
   const bool mx = ctx->mixed;
   const SchedView &A8 = ctx->sa8.view, &T8 = ctx->st8.view;
@@ -217,6 +222,10 @@ static pdhg_status fixed_schedules(pdhg_ctx* ctx) {
   ctx->partials_len = (size_t)(gmax + long_rows + 1) * kEvalQ;
   CKS(dalloc(ctx, &ctx->partials, ctx->partials_len));
   CKS(dalloc(ctx, &ctx->split_q, (size_t)(long_rows + 1) * kEvalQ));
+  // the adaptive step's sums: one per primal block and split row of A~^T,
+  // two per dual block and split row of A~, for any candidate schedule
+  if (ctx->opt.step_rule == 1 && !ctx->batch)
+    CKS(dalloc(ctx, &ctx->adapt_sums, 3 * (size_t)ctx->nsm * 8 + 2 * ((size_t)long_rows + 1)));
   return PDHG_OK;
 }
 
@@ -391,9 +400,25 @@ static void enqueue_chunk_any(pdhg_ctx* ctx, int len, cudaEvent_t* timing) {
     enqueue_chunk<double>(ctx, len, timing);
 }
 
+// The adaptive step's launch of one half-step on schedule S (its dual
+// gathers the pairs (x+, x): the shared memory of two vectors).
+static void set_adaptive_launch(pdhg_ctx* ctx, bool on_a, const SchedView& S) {
+  if (ctx->opt.step_rule != 1 || ctx->batch) return;
+  const bool mx = ctx->mixed;
+  const size_t sm = smem_for(on_a ? 1 : 0, mx, S.max_rows, S.e);
+  const int occ = adaptive_occupancy((on_a ? 2 : 0) + (mx ? 0 : 1), S.e, sm);
+  (on_a ? ctx->l_adual : ctx->l_aprim) = Launch{std::max(1, std::min(S.ntiles, ctx->nsm * occ)), sm};
+}
+static int half_launches(const pdhg_ctx* ctx, bool dual) {
+  if (ctx->opt.step_rule == 1) return dual ? 2 : 1;
+  return dual ? dual_launches(ctx) : prim_launches(ctx);
+}
+
 // Iteration schedules: every candidate is timed with the real fused primal
-// (rows of A~^T) or dual (rows of A~) kernel on the initial state; the state
-// is zeroed again afterwards.  Candidates: the segmented kernel with 8, 16
+// (rows of A~^T) or dual (rows of A~) kernel on the initial state (with the
+// adaptive step, its own half-steps: gathering two vectors changes which
+// schedule wins); the state is zeroed again afterwards, and the step state
+// the adaptive judge changed is put back.  Candidates: the segmented kernel with 8, 16
 // or 32 nonzeros per thread (a vector kernel with -e lanes per row, e < 0,
 // only when options.tile_nnz asks for it and all rows are short).  E = 8 is
 // kept unless another choice is more than 5% faster, so timing noise does not
@@ -405,13 +430,13 @@ static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const int warm = 3, reps = 10;
-  ctx->launches += (long long)(warm + reps) * (on_a ? dual_launches(ctx) : prim_launches(ctx));
+  ctx->launches += (long long)(warm + reps) * half_launches(ctx, on_a);
   for (int it = 0; it < warm + reps; ++it) {
     if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
     if (on_a)
-      launch_dual_step<T>(ctx, B, 0);
+      launch_dual_half<T>(ctx, B, 0);
     else
-      launch_prim_step<T>(ctx, B, 0);
+      launch_prim_half<T>(ctx, B, 0);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(e1, ctx->stream));
@@ -456,6 +481,9 @@ constexpr int kLongWindowRows = 8;
 
 static pdhg_status tune_schedules(pdhg_ctx* ctx) {
   const bool mx = ctx->mixed;
+  Scalars sc0{};  // the adaptive judge moves the step state while candidates run
+  CK(cudaMemcpyAsync(&sc0, ctx->sc, sizeof(sc0), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   for (int which = 0; which < 2; ++which) {
     const bool on_a = which == 0;
     const std::vector<int32_t>& rp = on_a ? ctx->h_a_rp : ctx->h_t_rp;
@@ -498,6 +526,7 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
       else
         ctx->l_prim = make_launch(ctx, prim_kind(ctx), d.view.e,
                                   smem_for(0, mx, d.view.max_rows, d.view.e), d.view.ntiles);
+      set_adaptive_launch(ctx, on_a, d.view);
       float ms = 0.f;
       if (cands.size() > 1) {
         if (mx)
@@ -521,6 +550,7 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
     else
       ctx->l_prim = make_launch(ctx, prim_kind(ctx), best.view.e,
                                 smem_for(0, mx, best.view.max_rows, best.view.e), best.view.ntiles);
+    set_adaptive_launch(ctx, on_a, best.view);
 
     // column panels where they apply: forced (spmv_layout 2), or candidates
     // timed below against the CSR tiles picked above (autotune on, tile_nnz 0,
@@ -580,22 +610,8 @@ static pdhg_status tune_schedules(pdhg_ctx* ctx) {
     CK(cudaMemsetAsync(p, 0, es * ctx->n, ctx->stream));
   for (void* p : {ctx->y, ctx->y_avg, ctx->y_last, ctx->Ax, ctx->Ax_avg, ctx->Ax_last})
     CK(cudaMemsetAsync(p, 0, es * ctx->m, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->sc, &sc0, sizeof(sc0), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  return PDHG_OK;
-}
-
-// Launches of the adaptive half-steps on the tuned schedules (the dual
-// gathers x+ and the move together) and the attempt's sums: one per primal
-// block and split row of A~^T, two per dual block and split row of A~.
-static pdhg_status adaptive_launches(pdhg_ctx* ctx) {
-  if (ctx->opt.step_rule != 1 || ctx->batch) return PDHG_OK;
-  const bool mx = ctx->mixed;
-  const SchedView &A = ctx->sa.view, &T = ctx->st.view;
-  const size_t sp = smem_for(0, mx, T.max_rows, T.e), sd = smem_for(1, mx, A.max_rows, A.e);
-  ctx->l_aprim = Launch{std::max(1, std::min(T.ntiles, ctx->nsm * adaptive_occupancy(mx ? 0 : 1, T.e, sp))), sp};
-  ctx->l_adual = Launch{std::max(1, std::min(A.ntiles, ctx->nsm * adaptive_occupancy(mx ? 2 : 3, A.e, sd))), sd};
-  const size_t len = (size_t)ctx->l_aprim.grid + T.ngroups + 2 * ((size_t)ctx->l_adual.grid + A.ngroups);
-  CKS(dalloc(ctx, &ctx->adapt_sums, len));
   return PDHG_OK;
 }
 
@@ -717,6 +733,7 @@ pdhg_status pdhg::alloc_arrays(pdhg_ctx* ctx) {
   if (ctx->opt.step_rule == 1 && !ctx->batch) {
     CKS(dalloc(ctx, (char**)&ctx->x_avg_prev, es * n));
     CKS(dalloc(ctx, (char**)&ctx->adapt_xx, es * 2 * (size_t)n));
+    CK(cudaMemsetAsync(ctx->adapt_xx, 0, es * 2 * (size_t)n, ctx->stream));
     for (void** p : {&ctx->y_prev, &ctx->y_avg_prev, &ctx->Ax_prev, &ctx->Ax_avg_prev})
       CKS(dalloc(ctx, (char**)p, es * m));
   }
@@ -1003,7 +1020,6 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
 
   stage("scalars");
   CKS(tune_schedules(ctx));
-  CKS(adaptive_launches(ctx));
   stage("schedule tuning");
   CKS(polling_resources(ctx));
   stage("polling resources");

@@ -60,6 +60,30 @@ def dense_column_lp(seed=0):
                     x, y, z, name="dense_columns")
 
 
+def mid_column_lp(seed=0):
+    """Columns of 150 to 1500 entries: shorter than a full tile of 8
+    nonzeros per thread (2044), longer than the reduced tile capacities a
+    forced tile_nnz may ask for, so those schedules split rows of A^T that
+    the full capacity keeps whole (the split records of the evaluation must
+    cover them)."""
+    rng = np.random.default_rng(seed)
+    m, n = 3000, 400
+    rows, cols = [], []
+    for j in range(n):
+        k = [150, 600, 1500][j % 3] if j < 60 else int(rng.integers(2, 7))
+        rows.append(rng.choice(m, size=k, replace=False))
+        cols.append(np.full(k, j))
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    A = sp.csr_matrix((rng.standard_normal(rows.size), (rows, cols)), shape=(m, n))
+    A.sort_indices()
+    x = rng.uniform(0.5, 2, n) * (rng.random(n) < 0.3)
+    y = rng.standard_normal(m)
+    z = np.where(x > 0, 0.0, rng.uniform(0.5, 2, n))
+    return lpgen.LP(m, n, A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.copy(),
+                    A @ x, A.T @ y + z, x, y, z, name="mid_columns")
+
+
 def heavy_row_lp(seed=0):
     """Power-law rows with some rows longer than every tile size (split rows)."""
     return lpgen.powerlaw_lp(m=3000, n=12000, nnz=90000, k_max=9000, seed=seed)
@@ -139,7 +163,7 @@ def _compare_state(st, ost, tol):
 # the vector variant (falls back to segmented where rows exceed 256)
 @pytest.mark.parametrize("tile_nnz", [0, 100, 512, 1371, 3000, 8000, -4, -8])
 @pytest.mark.parametrize("maker", [lambda: lpgen.planted_lp(200, 500, seed=0), heavy_row_lp,
-                                   dense_column_lp, gappy_lp])
+                                   dense_column_lp, gappy_lp, mid_column_lp])
 def test_fp64_iterates_after_100(maker, tile_nnz):
     lp = maker()
     r = O.solve(lp, 1e-12, 100)
