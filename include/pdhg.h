@@ -298,10 +298,10 @@ pdhg_status pdhg_get_kernel_timing_parts(pdhg_ctx* ctx, double* ms, int64_t* sam
  * alone, 4: that of the dual half-step (3, 4: 0 on the CSR tiles, where a
  * half-step is one fused kernel)}, timed with CUDA events on the context's
  * stream on its current iterate.  With options.step_rule = 1 the half-steps
- * are the adaptive step's own: the primal also saves the accepted x and
- * writes the move, the dual also forms A~ times the move and judges the
- * attempt, followed by the kernel that undoes a rejected attempt (timed with
- * the dual).  Launches are back to back as in a solve
+ * are the adaptive step's own: the primal also saves the accepted state
+ * and writes the attempt's x beside it, the dual also forms A~ times the
+ * move and applies the acceptance test, followed by the kernel that undoes a
+ * rejected attempt (timed with the dual).  Launches are back to back as in a solve
  * (programmatic dependent launch), with no event between them.  The solver
  * state is saved to a temporary device buffer first and restored after, so
  * a solve continues as if the call had not happened.  Single-LP contexts.  */

@@ -208,7 +208,7 @@ size_t tile_smem(int nv, bool f32, int max_rows, int e);
 
 // ---- adaptive step (adaptive.cu) ------------------------------------------
 // attempt i of the chunk: the primal half-step saving the accepted state, the
-// dual half-step with the judge of the attempt, and the undo of a rejected one
+// dual half-step with the acceptance test of the attempt, and the undo of a rejected one
 template <typename T>
 void launch_adapt_primal(const IterBuffers<T>& B, const Launch& L, int i, cudaStream_t s);
 template <typename T>

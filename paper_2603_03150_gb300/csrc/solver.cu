@@ -327,7 +327,7 @@ static void launch_dual_step(pdhg_ctx* ctx, const IterBuffers<T>& B, int i,
   if (between) cudaEventRecordWithFlags(between, ctx->stream, cudaEventRecordExternal);
 }
 // the half-steps a solve runs: the adaptive step's own kernels (its dual
-// half-step ends with the judge of the attempt, then the undo of a rejected
+// half-step ends with the acceptance test of the attempt, then the undo of a rejected
 // one), else the above
 template <typename T>
 static void launch_prim_half(pdhg_ctx* ctx, const IterBuffers<T>& B, int i,
@@ -418,7 +418,7 @@ static int half_launches(const pdhg_ctx* ctx, bool dual) {
 // (rows of A~^T) or dual (rows of A~) kernel on the initial state (with the
 // adaptive step, its own half-steps: gathering two vectors changes which
 // schedule wins); the state is zeroed again afterwards, and the step state
-// the adaptive judge changed is put back.  Candidates: the segmented kernel with 8, 16
+// the adaptive acceptance test changed is put back.  Candidates: the segmented kernel with 8, 16
 // or 32 nonzeros per thread (a vector kernel with -e lanes per row, e < 0,
 // only when options.tile_nnz asks for it and all rows are short).  E = 8 is
 // kept unless another choice is more than 5% faster, so timing noise does not
@@ -481,7 +481,7 @@ constexpr int kLongWindowRows = 8;
 
 static pdhg_status tune_schedules(pdhg_ctx* ctx) {
   const bool mx = ctx->mixed;
-  Scalars sc0{};  // the adaptive judge moves the step state while candidates run
+  Scalars sc0{};  // the adaptive acceptance test moves the step state while candidates run
   CK(cudaMemcpyAsync(&sc0, ctx->sc, sizeof(sc0), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int which = 0; which < 2; ++which) {
