@@ -268,40 +268,90 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
 // then the half-step's row epilogue.
 // G = 0 (up to 32 panels, rows enough for 4 per thread on every SM): a
 // thread takes 4 consecutive rows with 16-byte loads of each panel's 4 sums
-// and of the epilogue's operands (loaded before the sums arrive); rows past
-// the last multiple of 4 one per thread.
+// and of the epilogue's operands; rows past the last multiple of 4 one per
+// thread.
 // G >= 1: G consecutive lanes share a row: lane k adds its contiguous share
 // of the panels in order (8 loads in flight per round), lane 0 adds the
 // shares in lane order; warps stride over groups of 32 / G rows.
+// The step's scalars (read by thread 0 into rs) are needed only to apply the
+// epilogue: each thread first loads and adds its first rows' operands and
+// sums, then meets the block barrier that publishes rs, so those loads
+// overlap thread 0's read.  The epilogue is built with first = false (its
+// loads do not skip the running average) and gets the scalars after the
+// barrier.
+
+// the step's scalars into the epilogue: a = tau or sigma, b = the averaging
+// weight (or lam of the Halpern method)
+struct RowScalars {
+  float a, b;
+  int first, done;
+};
+__device__ __forceinline__ void set_step(PrimalEpi<float>& e, const RowScalars& r) {
+  e.tau = r.a;
+  e.w = r.b;
+  e.first = r.first != 0;
+}
+__device__ __forceinline__ void set_step(DualEpi<float>& e, const RowScalars& r) {
+  e.sigma = r.a;
+  e.w = r.b;
+  e.first = r.first != 0;
+}
+__device__ __forceinline__ void set_step(HalpernPrimalEpi<float>& e, const RowScalars& r) {
+  e.tau = r.a;
+  e.lam = r.b;
+}
+__device__ __forceinline__ void set_step(HalpernDualEpi<float>& e, const RowScalars& r) {
+  e.sigma = r.a;
+  e.lam = r.b;
+}
+
+// the panels' sums of rows i..i+3, added in panel order
+__device__ __forceinline__ float4 sum4(const PanelView& V, int i) {
+  const int np = V.npanels;
+  const size_t stride = (size_t)V.pstride;
+  const float* pp = V.partial + i;
+  float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = 0; c < np; c += 8) {
+    float4 u[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      u[r] = c + r < np ? __ldcg(reinterpret_cast<const float4*>(pp + (size_t)(c + r) * stride))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      if (c + r < np) {
+        t.x += u[r].x;
+        t.y += u[r].y;
+        t.z += u[r].z;
+        t.w += u[r].w;
+      }
+  }
+  return t;
+}
+
 template <int G, class Epi>
-__device__ __forceinline__ void panel_rows(const PanelView& V, Epi& epi) {
+__device__ __forceinline__ void panel_rows(const PanelView& V, Epi& epi, const RowScalars* rs) {
   const int rows = V.rows, np = V.npanels;
   const size_t stride = (size_t)V.pstride;
   if constexpr (G == 0) {
     const int nthr = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int n4 = rows >> 2;
-    for (int q = tid; q < n4; q += nthr) {
+    // the first quad of rows before the barrier
+    typename Epi::In4 in0{};
+    float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < n4) {
+      in0 = epi.load4(tid << 2);
+      t0 = sum4(V, tid << 2);
+    }
+    __syncthreads();
+    if (rs->done) return;
+    set_step(epi, *rs);
+    if (tid < n4) epi.apply4(tid << 2, in0, t0);
+    for (int q = tid + nthr; q < n4; q += nthr) {
       const int i = q << 2;
       const typename Epi::In4 in = epi.load4(i);
-      const float* pp = V.partial + i;
-      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int c = 0; c < np; c += 8) {
-        float4 u[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-          u[r] = c + r < np ? __ldcg(reinterpret_cast<const float4*>(pp + (size_t)(c + r) * stride))
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-          if (c + r < np) {
-            t.x += u[r].x;
-            t.y += u[r].y;
-            t.z += u[r].z;
-            t.w += u[r].w;
-          }
-      }
-      epi.apply4(i, in, t);
+      epi.apply4(i, in, sum4(V, i));
     }
     for (int i = (n4 << 2) + tid; i < rows; i += nthr) {
       const typename Epi::In in = epi.load(i);
@@ -316,11 +366,11 @@ __device__ __forceinline__ void panel_rows(const PanelView& V, Epi& epi) {
     const float* __restrict__ part = V.partial + (size_t)(k * per) * stride;
     constexpr int kRowsPerWarp = 32 / G;
     const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int r0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kRowsPerWarp; r0 < rows;
-         r0 += nw * kRowsPerWarp) {
-      const int i = r0 + lane / G;
+    int r0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kRowsPerWarp;
+    // one group of rows: the epilogue's operands and the row's sum (in lane 0 of the row)
+    auto group = [&](int rr0, typename Epi::In& in, float& s) {
+      const int i = rr0 + lane / G;
       const bool live = i < rows;
-      typename Epi::In in{};
       if (live && k == 0) in = epi.load(i);
       float t = 0.f;
       const float* pp = part + i;
@@ -332,25 +382,34 @@ __device__ __forceinline__ void panel_rows(const PanelView& V, Epi& epi) {
         for (int r = 0; r < 8; ++r)
           if (c + r < mine) t += q[r];
       }
-      float s = t;
+      s = t;
 #pragma unroll
       for (int o = 1; o < G; ++o) {
         const float u = __shfl_sync(0xffffffffu, t, base_lane + o);
         if (k == 0) s += u;
       }
-      if (live && k == 0) epi.apply(i, in, s);
+    };
+    typename Epi::In in0{};
+    float s0 = 0.f;
+    if (r0 < rows) group(r0, in0, s0);  // warp-uniform
+    __syncthreads();
+    if (rs->done) return;
+    set_step(epi, *rs);
+    if (r0 < rows && r0 + lane / G < rows && k == 0) epi.apply(r0 + lane / G, in0, s0);
+    for (r0 += nw * kRowsPerWarp; r0 < rows; r0 += nw * kRowsPerWarp) {
+      typename Epi::In in{};
+      float s = 0.f;
+      group(r0, in, s);
+      const int i = r0 + lane / G;
+      if (i < rows && k == 0) epi.apply(i, in, s);
     }
   }
 }
 
-// The step's scalars, read from the device state once per block: a = tau or
-// sigma, b = the averaging weight 1/(t+1) (or lam of the Halpern method),
-// first = no average yet, done = the solve has finished.
-struct RowScalars {
-  float a, b;
-  int first, done;
-};
-
+// The step's scalars, read from the device state by thread 0 (no barrier:
+// panel_rows meets it after its first loads): a = tau or sigma, b = the
+// averaging weight 1/(t+1) (or lam of the Halpern method), first = no
+// average yet, done = the solve has finished.
 __device__ __forceinline__ void row_scalars(const IterBuffers<float>& B, int i, bool dual,
                                             bool halpern, RowScalars* out) {
   if (threadIdx.x == 0) {
@@ -361,7 +420,6 @@ __device__ __forceinline__ void row_scalars(const IterBuffers<float>& B, int i, 
     out->b = halpern ? (float)((double)(tt + 1) / (double)(tt + 2)) : (float)(1.0 / (double)(tt + 1));
     out->first = tt == 0;
   }
-  __syncthreads();
 }
 
 template <int G>
@@ -376,9 +434,8 @@ __global__ void __launch_bounds__(256, 6) k_panel_primal(IterBuffers<float> B, P
   pdl_trigger();
   pdl_enter();
   row_scalars(B, i, false, false, &rs);
-  if (rs.done) return;
-  PrimalEpi<float> epi{B.x, B.c_t, B.x_avg, rs.a, rs.b, rs.first != 0};
-  panel_rows<G>(V, epi);
+  PrimalEpi<float> epi{B.x, B.c_t, B.x_avg, 0.f, 0.f, false};
+  panel_rows<G>(V, epi, &rs);
 }
 
 template <int G>
@@ -387,9 +444,8 @@ __global__ void __launch_bounds__(256, 6) k_panel_dual(IterBuffers<float> B, Pan
   pdl_trigger();
   pdl_enter();
   row_scalars(B, i, true, false, &rs);
-  if (rs.done) return;
-  DualEpi<float> epi{B.y, B.b_t, B.Ax, B.y_avg, B.Ax_avg, rs.a, rs.b, rs.first != 0};
-  panel_rows<G>(V, epi);
+  DualEpi<float> epi{B.y, B.b_t, B.Ax, B.y_avg, B.Ax_avg, 0.f, 0.f, false};
+  panel_rows<G>(V, epi, &rs);
 }
 
 template <int G>
@@ -398,9 +454,8 @@ __global__ void __launch_bounds__(256, 6) k_panel_hprimal(IterBuffers<float> B, 
   pdl_trigger();
   pdl_enter();
   row_scalars(B, i, false, true, &rs);
-  if (rs.done) return;
-  HalpernPrimalEpi<float> epi{B.x, B.x_avg, B.c_t, B.x_last, rs.a, rs.b, (float)B.rho};
-  panel_rows<G>(V, epi);
+  HalpernPrimalEpi<float> epi{B.x, B.x_avg, B.c_t, B.x_last, 0.f, 0.f, (float)B.rho};
+  panel_rows<G>(V, epi, &rs);
 }
 
 template <int G>
@@ -409,10 +464,9 @@ __global__ void __launch_bounds__(256, 6) k_panel_hdual(IterBuffers<float> B, Pa
   pdl_trigger();
   pdl_enter();
   row_scalars(B, i, true, true, &rs);
-  if (rs.done) return;
   HalpernDualEpi<float> epi{B.y,      B.b_t,     B.Ax, B.y_avg, B.Ax_avg,
-                            B.y_last, B.Ax_last, rs.a, rs.b,    (float)B.rho};
-  panel_rows<G>(V, epi);
+                            B.y_last, B.Ax_last, 0.f,  0.f,     (float)B.rho};
+  panel_rows<G>(V, epi, &rs);
 }
 
 // lanes per row: one up to 32 panels (each costs a lane a load and an add,
