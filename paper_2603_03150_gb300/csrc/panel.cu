@@ -128,7 +128,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   PanelLoad cur;  // the first tile's loads go out before the wait
   if (t < bd.t_end) panel_load(cur, V, dc, bd.t_begin, t, lane, pol);
   pdl_enter();
-  if (sc->done) return;
   {
     // the panel of v: whole 16-byte pieces by the bulk-copy engine (one
     // thread issues 32 KB copies onto the transaction barrier), the tail by
@@ -136,7 +135,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     // and so does its place in shared memory.  The wait is bounded
     // (options.wait_limit_ms): past it the block flags the error, waits once
     // more for its copies in flight, and returns without its work (the solve
-    // reports a timeout).
+    // reports a timeout).  Whether the solve has finished is read while the
+    // copies run; a finished solve returns once they have landed (no block
+    // exits with a copy into its shared memory in flight).
     const int c0 = bd.panel * V.P;
     const int cnt = min(V.P, V.cols - c0);
     const uint32_t bytes = ((uint32_t)cnt * 4u) & ~15u;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       constexpr uint32_t kPiece = 32768;
       for (uint32_t o = 0; o < bytes; o += kPiece) bulk_copy_g2s(dst + o, src + o, min(kPiece, bytes - o), mb);
     }
+    const int done = sc->done;  // not written while this kernel runs: the same in every thread
     for (int q = (int)(bytes >> 2) + tid; q < cnt; q += kPanelThreads) vs[q] = __ldg(v + c0 + q);
     const bool ok = mbar_wait(mb, 0, V.wait_ns);
     if (__syncthreads_or(!ok)) {
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       mbar_wait(mb, 0, V.wait_ns);
       return;
     }
+    if (done) return;
   }
   float* st = stage + warp * V.pscap;
   float* part = V.partial + (size_t)bd.panel * V.pstride;
