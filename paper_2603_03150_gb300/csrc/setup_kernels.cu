@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <math.h>
 
+#include "dispatch.cuh"
 #include "kernels.h"
 #include "spmv_tile.cuh"
 
@@ -436,7 +437,9 @@ void launch_sum_final(const double* partials, int g, double* out, cudaStream_t s
 }
 
 // ---------------------------------------------------------------------------
-// power iteration on A~^T A~ (float64)
+// power iteration on A~^T A~ (float64).  Its three kernels are launched with
+// programmatic dependent launch and wait on entry, so each launch is set up
+// while the previous kernel drains.
 // ---------------------------------------------------------------------------
 __global__ void k_pow_init(int n, double* v, PowerState* ps, int max_iter, double rel_tol) {
   const double v0 = 1.0 / sqrt((double)n);
@@ -461,6 +464,7 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_pow_Av(SchedView S, const int32_t* rp, const int32_t* col,
                                                  const double* val, const double* v, double* u,
                                                  const PowerState* ps) {
+  pdl_enter();
   if (ps->stopped) return;
   extern __shared__ __align__(16) unsigned char smem[];
   struct E {
@@ -493,6 +497,7 @@ __global__ void __launch_bounds__(BLOCK) k_pow_ATu(SchedView S, const int32_t* r
                                                   const double* val, const double* u,
                                                   const double* v, double* w, double* partials,
                                                   PowerState* ps, int ngroups) {
+  pdl_enter();
   if (ps->stopped) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[2 * (BLOCK / 32)];
@@ -533,6 +538,7 @@ __global__ void __launch_bounds__(BLOCK) k_pow_ATu(SchedView S, const int32_t* r
 }
 
 __global__ void k_pow_norm(int n, const double* w, double* v, const PowerState* ps) {
+  pdl_enter();
   const double s = ps->inv_norm;
   if (s == 0.0) return;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) v[j] = w[j] * s;
@@ -540,16 +546,16 @@ __global__ void k_pow_norm(int n, const double* w, double* v, const PowerState* 
 
 void launch_pow_Av(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
                    const double* v, double* u, PowerState* ps, const Launch& L, cudaStream_t s) {
-  k_pow_Av<kBlock><<<L.grid, kBlock, L.smem, s>>>(S, rp, col, val, v, u, ps);
+  launch_pdl(k_pow_Av<kBlock>, L.grid, kBlock, L.smem, s, S, rp, col, val, v, u, (const PowerState*)ps);
 }
 void launch_pow_ATu(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
                     const double* u, const double* v, double* w, double* partials,
                     PowerState* ps, const Launch& L, cudaStream_t s) {
-  k_pow_ATu<kBlock><<<L.grid, kBlock, L.smem, s>>>(S, rp, col, val, u, v, w, partials, ps,
-                                                   S.ngroups);
+  launch_pdl(k_pow_ATu<kBlock>, L.grid, kBlock, L.smem, s, S, rp, col, val, u, v, w, partials, ps,
+             (int)S.ngroups);
 }
 void launch_pow_norm(int n, const double* w, double* v, PowerState* ps, cudaStream_t s) {
-  k_pow_norm<<<grid_cap(n), 256, 0, s>>>(n, w, v, ps);
+  launch_pdl(k_pow_norm, grid_cap(n), 256, 0, s, n, w, v, (const PowerState*)ps);
 }
 
 // sums: |b|^2, |c|^2, |b~|^2, |c~|^2, |min(0, c~)|^2
