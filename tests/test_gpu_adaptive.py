@@ -23,7 +23,7 @@ from oracle import pdhg_oracle as O
 from paper_2603_03150_gb300 import build as B
 from paper_2603_03150_gb300 import lpgen, pdhg
 
-from test_gpu_parity import gappy_lp, heavy_row_lp, rel_inf
+from test_gpu_parity import gappy_lp, heavy_row_lp, mid_column_lp, rel_inf
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +74,21 @@ def test_adaptive_iterates_after_72_match_oracle(maker):
     _compare(st, r)
     assert [(e["k"], e["restart"], e["cand"]) for e in lg] == \
            [(e["k"], e["restart"], e["cand"]) for e in r.log]
+
+
+@pytest.mark.parametrize("maker", [mid_column_lp, gappy_lp])
+def test_adaptive_split_rows_at_a_small_tile_capacity(maker):
+    """tile_nnz = 100 splits rows of both matrices across tiles (rows of A~^T
+    of 150 to 1500 entries on the first LP): every split row's terms of the
+    attempt's sums have a record of their own; iterates after 72 attempts as
+    in the oracle."""
+    lp = maker()
+    opts = O.Options(step_rule="adaptive")
+    with pdhg.Solver.from_lp(lp, step_rule="adaptive", tile_nnz=100) as s:
+        r = O.solve(lp, 1e-12, 72, opts=opts, S=_setup_from(s, lp))
+        assert s.solve(1e-12, 72) == pdhg.PDHG_MAX_ITER
+        st = s.state()
+    _compare(st, r)
 
 
 def test_forced_rejection_is_undone_as_in_the_oracle():
