@@ -418,11 +418,12 @@ static int half_launches(const pdhg_ctx* ctx, bool dual) {
 // (rows of A~^T) or dual (rows of A~) kernel on the initial state (with the
 // adaptive step, its own half-steps: gathering two vectors changes which
 // schedule wins); the state is zeroed again afterwards, and the step state
-// the adaptive acceptance test changed is put back.  Candidates: the segmented kernel with 8, 16
-// or 32 nonzeros per thread (a vector kernel with -e lanes per row, e < 0,
-// only when options.tile_nnz asks for it and all rows are short).  E = 8 is
-// kept unless another choice is more than 5% faster, so timing noise does not
-// flip the schedule from one context to the next.
+// the adaptive acceptance test changed is put back.  Candidates: the
+// segmented kernel with 8, 16 or 32 nonzeros per thread (a vector kernel
+// with -e lanes per row, e < 0, only when options.tile_nnz asks for it and
+// all rows are short).  E = 8 is kept unless another choice is more than 5%
+// faster, so timing noise does not flip the schedule from one context to the
+// next.
 template <typename T>
 static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out) {
   const IterBuffers<T> B = iter_buffers<T>(ctx);
