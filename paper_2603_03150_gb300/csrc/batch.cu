@@ -21,6 +21,53 @@ namespace pdhg {
 constexpr int kRecP = 2;  // power-iteration record: v.w, |w|^2
 constexpr int kRecR = 4;  // report record
 
+// One tile's record: the block's sums of NQ float64 quantities (each thread
+// holds its share in v), written to out[0..NQ) by threads 0..NQ-1.  Within a
+// warp the sums are reduce-scattered: at each of the five shuffle steps a lane
+// keeps half of the quantities it still holds and adds its partner's half of
+// the same ones (then, one quantity left, the partner's value), so a lane adds
+// NQ + 1 values rather than 5 NQ: on GB300's slow float64 pipe this, not the
+// tile's SpMV, bounded the per-tile records.  Lane l ends with the warp's sum
+// of quantity l >> (5 - log2 NQ); the warps' sums are added in warp order.
+// The order is fixed, so records do not depend on scheduling.  Called by every
+// thread of the block; ends with a block barrier.
+template <int NQ>
+constexpr int log2_of() {
+  return NQ <= 1 ? 0 : 1 + log2_of<NQ / 2>();
+}
+template <int BLOCK, int NQ>
+__device__ __forceinline__ void tile_record(double (&v)[NQ], double* red, double* out) {
+  static_assert(NQ >= 1 && NQ <= 32 && (NQ & (NQ - 1)) == 0 && BLOCK % 32 == 0, "NQ");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int o = 16 >> st;
+    if ((NQ >> st) >= 2) {
+      const int half = (NQ >> st) / 2;
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < NQ / 2; ++k) {
+        if (k < half) {
+          const double send = up ? v[k] : v[k + half];
+          const double keep = up ? v[k + half] : v[k];
+          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+  constexpr int kShift = 5 - log2_of<NQ>();
+  if ((lane & ((1 << kShift) - 1)) == 0) red[w * NQ + (lane >> kShift)] = v[0];
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double t = 0.0;
+    for (int q = 0; q < BLOCK / 32; ++q) t += red[q * NQ + threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
 template <typename T>
 struct BatchBuffers {
   IterBuffers<T> it;  // it.sc: per-LP scalars [count]
@@ -153,15 +200,12 @@ struct BEvalEpi {
     }
   }
   __device__ __forceinline__ void end_tile(const Tile&, int t) {
-    double mine[kEvalQ], out[kEvalQ];
+    double mine[kEvalQ];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
       for (int k = 0; k < Q_N; ++k) mine[c * Q_N + k] = q[c][k];
-    block_sum<BLOCK, kEvalQ>(mine, out, red);
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int k = 0; k < kEvalQ; ++k) rec[(size_t)t * kEvalQ + k] = out[k];
+    tile_record<BLOCK, kEvalQ>(mine, red, rec + (size_t)t * kEvalQ);
   }
 };
 
@@ -195,11 +239,7 @@ __device__ __forceinline__ void beval_body(const BatchBuffers<T>& B, int chunk, 
         }
       }
     }
-    double out[kEvalQ];
-    block_sum<BLOCK, kEvalQ>(q, out, red);
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int k = 0; k < kEvalQ; ++k) B.rec_a[(size_t)t * kEvalQ + k] = out[k];
+    tile_record<BLOCK, kEvalQ>(q, red, B.rec_a + (size_t)t * kEvalQ);
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -313,13 +353,8 @@ struct BPowATuEpi {
     nw2 += s[0] * s[0];
   }
   __device__ __forceinline__ void end_tile(const Tile&, int t) {
-    const double mine[kRecP] = {lam, nw2};
-    double out[kRecP];
-    block_sum<BLOCK, kRecP>(mine, out, red);
-    if (threadIdx.x == 0) {
-      rec[(size_t)t * kRecP] = out[0];
-      rec[(size_t)t * kRecP + 1] = out[1];
-    }
+    double mine[kRecP] = {lam, nw2};
+    tile_record<BLOCK, kRecP>(mine, red, rec + (size_t)t * kRecP);
   }
 };
 
