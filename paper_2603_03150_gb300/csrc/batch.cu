@@ -21,51 +21,13 @@ namespace pdhg {
 constexpr int kRecP = 2;  // power-iteration record: v.w, |w|^2
 constexpr int kRecR = 4;  // report record
 
-// One tile's record: the block's sums of NQ float64 quantities (each thread
-// holds its share in v), written to out[0..NQ) by threads 0..NQ-1.  Within a
-// warp the sums are reduce-scattered: at each of the five shuffle steps a lane
-// keeps half of the quantities it still holds and adds its partner's half of
-// the same ones (then, one quantity left, the partner's value), so a lane adds
-// NQ + 1 values rather than 5 NQ: on GB300's slow float64 pipe this, not the
-// tile's SpMV, bounded the per-tile records.  Lane l ends with the warp's sum
-// of quantity l >> (5 - log2 NQ); the warps' sums are added in warp order.
-// The order is fixed, so records do not depend on scheduling.  Called by every
-// thread of the block; ends with a block barrier.
-template <int NQ>
-constexpr int log2_of() {
-  return NQ <= 1 ? 0 : 1 + log2_of<NQ / 2>();
-}
+// One tile's record (the block's sums of NQ float64 quantities, written by
+// threads 0..NQ-1): block_sum_scatter's reduce-scatter order.  Every lane
+// adding all NQ quantities at each shuffle step, on GB300's slow float64
+// pipe, had bounded the per-tile records.
 template <int BLOCK, int NQ>
 __device__ __forceinline__ void tile_record(double (&v)[NQ], double* red, double* out) {
-  static_assert(NQ >= 1 && NQ <= 32 && (NQ & (NQ - 1)) == 0 && BLOCK % 32 == 0, "NQ");
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int o = 16 >> st;
-    if ((NQ >> st) >= 2) {
-      const int half = (NQ >> st) / 2;
-      const bool up = (lane & o) != 0;
-#pragma unroll
-      for (int k = 0; k < NQ / 2; ++k) {
-        if (k < half) {
-          const double send = up ? v[k] : v[k + half];
-          const double keep = up ? v[k + half] : v[k];
-          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-      }
-    } else {
-      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
-    }
-  }
-  constexpr int kShift = 5 - log2_of<NQ>();
-  if ((lane & ((1 << kShift) - 1)) == 0) red[w * NQ + (lane >> kShift)] = v[0];
-  __syncthreads();
-  if (threadIdx.x < NQ) {
-    double t = 0.0;
-    for (int q = 0; q < BLOCK / 32; ++q) t += red[q * NQ + threadIdx.x];
-    out[threadIdx.x] = t;
-  }
-  __syncthreads();
+  block_sum_scatter<BLOCK, NQ>(v, red, out);
 }
 
 template <typename T>

@@ -129,15 +129,15 @@ __global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
       epi.q[c][Q_D2] += dy * dy;
     }
   }
-  double mine[kEvalQ], out[kEvalQ];
+  double mine[kEvalQ];
 #pragma unroll
   for (int c = 0; c < 2; ++c)
 #pragma unroll
     for (int k = 0; k < Q_N; ++k) mine[c * Q_N + k] = epi.q[c][k];
-  block_sum<BLOCK, kEvalQ>(mine, out, red);
+  // the block's record (16 sums), then the ticket: the barrier that ends
+  // block_sum_scatter orders its writers' stores before thread 0's fence
+  block_sum_scatter<BLOCK, kEvalQ>(mine, red, B.partials + (size_t)blockIdx.x * kEvalQ);
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < kEvalQ; ++k) B.partials[(size_t)blockIdx.x * kEvalQ + k] = out[k];
     __threadfence();
     is_last = (atomicAdd(&B.sc->ticket, 1) == (int)gridDim.x - 1);
   }
