@@ -99,8 +99,12 @@ struct EvalEpi {
   }
 };
 
+// Float32-mixed evaluations ask for 4 resident blocks per SM (64 registers,
+// no spill; 3 at the 76 it takes otherwise): the kernel is bound by the
+// float64 pipe at low occupancy, so more warps keep that pipe busier.  The
+// float64 variants would spill under that bound and keep the default.
 template <typename T, int BLOCK, int E>
-__global__ void __launch_bounds__(BLOCK) k_eval(IterBuffers<T> B, int chunk) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 4 : 1) k_eval(IterBuffers<T> B, int chunk) {
   if (B.sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kEvalQ * (BLOCK / 32)];
