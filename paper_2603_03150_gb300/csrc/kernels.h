@@ -168,6 +168,8 @@ void launch_pow_ATu(const SchedView& S, const int32_t* rp, const int32_t* col, c
 void launch_pow_Av(const SchedView& S, const int32_t* rp, const int32_t* col, const double* val,
                    const double* v, double* u, PowerState* ps, const Launch& L, cudaStream_t s);
 void launch_pow_norm(int n, const double* w, double* v, PowerState* ps, cudaStream_t s);
+// blocks per SM of the power iteration's SpMV kernels (at: the A~^T one)
+int pow_occupancy(bool at, size_t smem);
 // scalar set-up of the solve from reduced values
 //   sums[5] = |b|^2, |c|^2, |b~|^2, |c~|^2, |min(0, c~)|^2
 // eta = eta_safety / sigma_max, omega_0 = |c~|/|b~| (1 if either is 0),

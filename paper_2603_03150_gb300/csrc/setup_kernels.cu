@@ -554,6 +554,12 @@ void launch_pow_ATu(const SchedView& S, const int32_t* rp, const int32_t* col, c
   launch_pdl(k_pow_ATu<kBlock>, L.grid, kBlock, L.smem, s, S, rp, col, val, u, v, w, partials, ps,
              (int)S.ngroups);
 }
+int pow_occupancy(bool at, size_t smem) {
+  const void* f = at ? (const void*)k_pow_ATu<kBlock> : (const void*)k_pow_Av<kBlock>;
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kBlock, smem);
+  return nb < 1 ? 1 : nb;
+}
 void launch_pow_norm(int n, const double* w, double* v, PowerState* ps, cudaStream_t s) {
   launch_pdl(k_pow_norm, grid_cap(n), 256, 0, s, n, w, v, (const PowerState*)ps);
 }

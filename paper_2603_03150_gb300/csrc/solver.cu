@@ -430,7 +430,7 @@ static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int warm = 3, reps = 10;
+  const int warm = 2, reps = 6;
   ctx->launches += (long long)(warm + reps) * half_launches(ctx, on_a);
   for (int it = 0; it < warm + reps; ++it) {
     if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
@@ -450,15 +450,15 @@ static pdhg_status time_iteration_kernel(pdhg_ctx* ctx, bool on_a, float* ms_out
   return PDHG_OK;
 }
 
-// mean time of one whole iteration (primal then dual half-step) over 10,
-// after 3 untimed
+// mean time of one whole iteration (primal then dual half-step) over 6,
+// after 2 untimed
 template <typename T>
 static pdhg_status time_iterations(pdhg_ctx* ctx, float* ms_out) {
   const IterBuffers<T> B = iter_buffers<T>(ctx);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int warm = 3, reps = 10;
+  const int warm = 2, reps = 6;
   ctx->launches += (long long)(warm + reps) * (prim_launches(ctx) + dual_launches(ctx));
   for (int it = 0; it < warm + reps; ++it) {
     if (it == warm) CK(cudaEventRecord(e0, ctx->stream));
@@ -964,11 +964,17 @@ static pdhg_status create_impl(pdhg_ctx* ctx, const int32_t* row_ptr, const int3
     double *v = ctx->xs64, *u = ctx->ys64, *w = ctx->out_n2;
     launch_pow_init(n, v, ctx->ps, ctx->opt.power_max_iter, ctx->opt.power_rel_tol, ctx->stream);
     ctx->launches += 1;
+    // grids from the power kernels' own occupancy (the float64 report
+    // kernel's, which l_a64 / l_t64 follow, holds more registers)
+    const Launch la{std::max(1, std::min(ctx->sa8.view.ntiles, ctx->nsm * pow_occupancy(false, ctx->l_a64.smem))),
+                    ctx->l_a64.smem};
+    const Launch lt{std::max(1, std::min(ctx->st8.view.ntiles, ctx->nsm * pow_occupancy(true, ctx->l_t64.smem))),
+                    ctx->l_t64.smem};
     for (int it = 0; it < ctx->opt.power_max_iter; ++it) {
-      launch_pow_Av(ctx->sa8.view, ctx->a_rp, ctx->a_col, ctx->a_val64, v, u, ctx->ps, ctx->l_a64,
+      launch_pow_Av(ctx->sa8.view, ctx->a_rp, ctx->a_col, ctx->a_val64, v, u, ctx->ps, la,
                     ctx->stream);
       launch_pow_ATu(ctx->st8.view, ctx->t_rp, ctx->t_col, ctx->t_val64, u, v, w, ctx->partials,
-                     ctx->ps, ctx->l_t64, ctx->stream);
+                     ctx->ps, lt, ctx->stream);
       launch_pow_norm(n, w, v, ctx->ps, ctx->stream);
       ctx->launches += 3;
       if ((it & 15) == 15) {
